@@ -1,0 +1,223 @@
+/*
+ * goat.h -- C ABI of libgoat, a GB300 (sm_103a) implementation of the
+ * Frank-Wolfe hot path of GOAT (Saad-Eldin, Pedigo, Priebe, Vogelstein,
+ * "Graph Matching via Optimal Transport"): FAQ's relaxation of graph matching
+ * with the linear-assignment direction step replaced by entropic optimal
+ * transport (Sinkhorn).
+ *
+ * Problem (Sec. 2.1-2.2): for adjacency matrices A, B (n x n) find the
+ * permutation maximising f(P) = tr(A^T P B P^T), which minimises the number of
+ * edge disagreements ||A - P B P^T||_F^2 = ||A||^2 + ||B||^2 - 2 f(P).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are dense, row-major, leading dimension n, in DEVICE memory
+ *     unless the name ends in _host.  Vectors likewise.
+ *   - A and B are symmetric with a zero diagonal (simple undirected graphs).
+ *     With that, grad f(P) = A P B^T + A^T P B = 2 A P B.
+ *   - G denotes MINUS the gradient, G = -grad f(P) (so G <= 0 for
+ *     non-negative graphs); the direction step solves min_Q <Q, G> - eps H(Q).
+ *   - Sinkhorn duals (f, g) give Q_ij = exp((f_i + g_j - G_ij) / eps); Q has
+ *     all row and column sums equal to 1 (the Birkhoff polytope, Sec. 3.3).
+ *   - perm[i] is the vertex of B matched to vertex i of A (P[i][perm[i]] = 1).
+ *   - The step size alpha returned here is the weight of the new direction:
+ *     P_new = P + alpha (Q - P); the paper's alpha (the weight of P) is
+ *     1 - alpha.
+ *   - Every call is asynchronous on `stream` except where a host output is
+ *     written, in which case the call synchronises `stream` before returning.
+ *   - Errors: every entry point returns GOAT_OK (0) or a negative goat_status;
+ *     outputs are unspecified after an error.  No C++ exception crosses the
+ *     ABI.  Device-side waits and iterative loops are bounded; exhausting a
+ *     bound returns GOAT_ERR_NOT_CONVERGED or GOAT_ERR_TIMEOUT, never a hang.
+ *   - Scratch memory: calls that need it take (workspace, workspace_bytes).
+ *     Pass a device buffer of at least goat_workspace_bytes(...) bytes, or
+ *     NULL, in which case the call allocates with cudaMallocAsync on `stream`
+ *     and frees before returning.  The caller owns all buffers it passes.
+ *   - The library computes only on the GPU.  It returns GOAT_ERR_UNSUPPORTED on
+ *     a device that is not compute capability 10.3; there is no CPU fallback.
+ */
+#ifndef GOAT_H_
+#define GOAT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GOAT_API __attribute__((visibility("default")))
+#else
+#define GOAT_API
+#endif
+
+/* CUDA stream handle (cudaStream_t); 0 is the legacy default stream. */
+typedef void *goat_stream_t;
+
+typedef enum goat_status {
+    GOAT_OK = 0,
+    GOAT_ERR_INVALID_ARG = -1,   /* bad size, null pointer, unsupported flag, asymmetric input */
+    GOAT_ERR_NOT_CONVERGED = -2, /* an iteration cap was reached where convergence is required */
+    GOAT_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+    GOAT_ERR_OUT_OF_MEMORY = -4, /* workspace too small or allocation failed */
+    GOAT_ERR_NAN = -5,           /* a non-finite value appeared in the iteration */
+    GOAT_ERR_TIMEOUT = -6,       /* a bounded device-side wait ran out */
+    GOAT_ERR_UNSUPPORTED = -7    /* device is not sm_103 */
+} goat_status;
+
+/* element type of the adjacency inputs */
+enum {
+    GOAT_DTYPE_U8 = 0,  /* uint8 0/1 entries */
+    GOAT_DTYPE_F32 = 1  /* float32 weights */
+};
+
+/* arithmetic of the two n x n x n gradient products */
+enum {
+    /* BF16 operands (exact for 0/1 adjacency), FP32 accumulation in TMEM; the
+     * intermediate Q B is rounded once to BF16.  Gradient error ~1e-3 relative. */
+    GOAT_PREC_BF16 = 0,
+    /* FP32-accurate: every non-adjacency operand is split into two BF16 terms
+     * (x = hi + lo), so each product runs twice the BF16 MMA work; error ~1e-6. */
+    GOAT_PREC_FP32 = 1
+};
+
+#define GOAT_TRACE_MAX 256
+
+typedef struct goat_params {
+    int precision;        /* GOAT_PREC_*, default GOAT_PREC_BF16                          */
+    int sk_max_iter;      /* Sinkhorn iterations per Frank-Wolfe step, default 500        */
+    float sk_tol;         /* Sinkhorn stop: max_j |column sum - 1| < sk_tol, default 1e-3 */
+    int sk_warm_start;    /* 1: start each Sinkhorn from the previous step's duals (default 1) */
+    int sk_check_every;   /* Sinkhorn iterations between host convergence checks, default 8 */
+    int project_on_grad;  /* 0: final LAP on P (default); 1: on grad f(P) (the paper's Alg. 3 line) */
+    int lap_max_rounds;   /* cap on auction bidding rounds over all phases, default 1<<20 */
+} goat_params;
+
+typedef struct goat_stats {
+    int fw_iters;                      /* Frank-Wolfe iterations run                         */
+    int converged;                     /* 1 if ||P_new - P||_F / sqrt(n) < tol ended the loop */
+    int sk_iters_total;                /* Sinkhorn iterations over all steps                */
+    int sk_iters[GOAT_TRACE_MAX];      /* per Frank-Wolfe step                              */
+    float sk_resid[GOAT_TRACE_MAX];    /* last marginal residual per step                  */
+    double alpha[GOAT_TRACE_MAX];      /* step size per step (weight of Q)                  */
+    double objective;                  /* f(perm), exact for 0/1 inputs                     */
+    double disagreements;              /* ||A||^2 + ||B||^2 - 2 f(perm)                     */
+    double lap_gap;                    /* dual - primal of the final LAP (0: certified)     */
+    int lap_rounds;                    /* auction rounds used                               */
+    float ms_total, ms_fw, ms_project; /* device time of the whole call, FW loop, projection */
+} goat_stats;
+
+/* Fills *p with the defaults listed above. */
+GOAT_API void goat_default_params(goat_params *p);
+
+/* Human-readable text for a goat_status.  Never NULL. */
+GOAT_API const char *goat_strerror(int status);
+
+/* Bytes of scratch the calls below need for size n (the maximum over calls).
+ * Returns 0 for n < 1. */
+GOAT_API size_t goat_workspace_bytes(int n, int dtype_AB, int precision);
+
+/*
+ * goat_match -- the whole GOAT solve (Alg. 3).
+ *   A, B       device, n x n, dtype_AB, symmetric, zero diagonal (checked:
+ *              GOAT_ERR_INVALID_ARG otherwise).
+ *   init       device n x n float doubly stochastic start, or NULL for the
+ *              barycenter J = 11^T / n (Alg. 3 "Initialize").
+ *   eps_rel    entropic weight per step: eps = eps_rel * max|grad f(P)|
+ *              (the paper's lambda = 1/eps, Sec. 3.3).
+ *   max_iter   Frank-Wolfe steps (>= 0), tol  stop when ||P_new-P||_F/sqrt(n) < tol.
+ *   p          parameters (NULL: defaults).
+ *   perm_out   HOST int32[n]; objective_out HOST double (nullable); stats HOST (nullable).
+ * Reaching max_iter is not an error.  Synchronises `stream`.
+ */
+GOAT_API int goat_match(const void *A, const void *B, int n, int dtype_AB, const float *init, float eps_rel, int max_iter,
+               float tol, const goat_params *p, int32_t *perm_out, double *objective_out, goat_stats *stats,
+               void *workspace, size_t workspace_bytes, goat_stream_t stream);
+
+/* goat_match with A, B, init in HOST memory (pageable or pinned); the copies to
+ * the device are part of the call. */
+GOAT_API int goat_match_host(const void *A_host, const void *B_host, int n, int dtype_AB, const float *init_host,
+                    float eps_rel, int max_iter, float tol, const goat_params *p, int32_t *perm_out,
+                    double *objective_out, goat_stats *stats, void *workspace, size_t workspace_bytes,
+                    goat_stream_t stream);
+
+/*
+ * goat_gradient -- Alg. 3 step 1: G_out = -grad f(P) = -(A P B^T + A^T P B) = -2 A P B.
+ *   A, B   device n x n (dtype_AB), symmetric.   P  device n x n float.
+ *   G_out  device n x n float.  precision  GOAT_PREC_*.
+ */
+GOAT_API int goat_gradient(const void *A, const void *B, int n, int dtype_AB, const float *P, float *G_out, int precision,
+                  void *workspace, size_t workspace_bytes, goat_stream_t stream);
+
+/*
+ * goat_sinkhorn -- LOT (Alg. 2): entropic rLAP min_Q <Q, G> - eps H(Q) over doubly
+ * stochastic Q, as log-domain Sinkhorn.  One iteration: row scaling
+ * f_i = -eps LSE_j((g_j - G_ij)/eps), then the column sums S_j of that Q,
+ * residual max_j |S_j - 1|, and the column scaling g_j -= eps log S_j.
+ *   G        device n x n float cost.          eps > 0.
+ *   f_out    device float[n].                  g_io  device float[n]: warm start in, duals out.
+ *   Q_out    device n x n float, or NULL.      stops when residual < tol or after max_iter.
+ *   iters_out, resid_out  HOST (nullable).  Reaching max_iter is not an error.
+ */
+GOAT_API int goat_sinkhorn(const float *G, int n, float eps, float tol, int max_iter, float *f_out, float *g_io,
+                  float *Q_out, int *iters_out, float *resid_out, void *workspace, size_t workspace_bytes,
+                  goat_stream_t stream);
+
+/*
+ * goat_line_search -- Alg. 3 step 3 (the exact quadratic step of FAQ / SGM).
+ * With D = Q - P, f(P + a D) = f(P) + b t + a t^2 where
+ *   b = <grad f(P), D> = -<G, D>,   a = tr(A^T D B D^T) = (1/2) <G - G_Q, D>,
+ * G = -grad f(P), G_Q = -grad f(Q) (grad f is linear, so grad f(D) = grad f(Q) - grad f(P)).
+ * alpha = argmax_{[0,1]} (maximize = 1) or argmin (maximize = 0) of b t + a t^2; when
+ * a >= 0 (resp. a <= 0) the end point 1 is taken only if strictly better than 0.
+ *   all matrices device n x n float;  alpha_out, a_out, b_out HOST (nullable except alpha_out).
+ */
+GOAT_API int goat_line_search(const float *G, const float *G_Q, const float *P, const float *Q, int n, int maximize,
+                     double *alpha_out, double *a_out, double *b_out, void *workspace, size_t workspace_bytes,
+                     goat_stream_t stream);
+
+/*
+ * goat_fw_update -- Alg. 3 step 4 and the gradient by linearity:
+ *   P <- P + alpha (Q - P),   G <- G + alpha (G_Q - G).
+ * All device n x n float; P and G are updated in place.
+ */
+GOAT_API int goat_fw_update(float *P, float *G, const float *Q, const float *G_Q, int n, double alpha, goat_stream_t stream);
+
+/*
+ * goat_project -- the final linear assignment (Alg. 3 return line):
+ * perm = argmax (maximize = 1) or argmin (0) of sum_i M[i][perm i] over permutations.
+ * GPU auction with eps-scaling, then an exact price-relaxation pass that
+ * either certifies the assignment optimal (LP duality) or repairs it.
+ *   M         device n x n float.     perm_out  device int32[n].
+ *   cost_out  HOST double: sum_i M[i][perm i] in FP64, row order (nullable).
+ *   gap_out   HOST double: dual minus primal after certification (nullable).
+ */
+GOAT_API int goat_project(const float *M, int n, int maximize, int32_t *perm_out, double *cost_out, double *gap_out,
+                 void *workspace, size_t workspace_bytes, goat_stream_t stream);
+
+/*
+ * goat_objective -- f(perm) = sum_ij A_ij B[perm i][perm j] (eq. QAP at a permutation)
+ * and disagreements ||A||^2 + ||B||^2 - 2 f.  Exact (64-bit integer sums) for
+ * GOAT_DTYPE_U8.  A, B, perm device; outputs HOST (nullable).
+ */
+GOAT_API int goat_objective(const void *A, const void *B, int n, int dtype_AB, const int32_t *perm, double *objective_out,
+                   double *disagreements_out, void *workspace, size_t workspace_bytes, goat_stream_t stream);
+
+/*
+ * goat_gemm_bf16_xyT -- kernel-level entry to the tensor-core product behind
+ * goat_gradient (Alg. 3 step 1 evaluates grad f with two such products):
+ *   out[r][c] = scale * sum_k X[r][k mod kx_period] * Y[c][k],  0 <= k < k_total.
+ *   X  device BF16, x_rows rows of x_stride elements (16-byte aligned rows);
+ *   Y  device BF16, y_rows rows of y_stride elements; k_total, kx_period multiples of 64;
+ *      rows or K positions beyond the given extents read as zero.
+ *   out  device float, out_rows x out_cols, leading dimension ld_out.
+ * Synchronises `stream`; GOAT_ERR_TIMEOUT if the kernel's bounded pipeline waits ran out.
+ */
+GOAT_API int goat_gemm_bf16_xyT(const void *X, int x_rows, int x_stride, int kx_period, const void *Y, int y_rows,
+                       int y_stride, int k_total, float scale, float *out, int ld_out, int out_rows, int out_cols,
+                       goat_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GOAT_H_ */

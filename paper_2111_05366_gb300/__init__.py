@@ -1,0 +1,322 @@
+"""GOAT (graph matching via optimal transport) on GB300: thin Python binding of libgoat.
+
+Every function here marshals torch CUDA tensors into the C ABI declared in
+``include/goat.h`` and calls it; all arithmetic runs in libgoat's sm_103a
+kernels.  There is no CPU fallback: if ``libgoat.so`` is missing or the device
+is not sm_103, the calls raise.
+
+Names follow the C ABI: ``goat_match``, ``goat_gradient``, ``goat_sinkhorn``,
+``goat_line_search``, ``goat_fw_update``, ``goat_project``, ``goat_objective``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgoat.so")
+
+GOAT_OK = 0
+GOAT_ERR_INVALID_ARG = -1
+GOAT_ERR_NOT_CONVERGED = -2
+GOAT_ERR_CUDA = -3
+GOAT_ERR_OUT_OF_MEMORY = -4
+GOAT_ERR_NAN = -5
+GOAT_ERR_TIMEOUT = -6
+GOAT_ERR_UNSUPPORTED = -7
+
+GOAT_DTYPE_U8 = 0
+GOAT_DTYPE_F32 = 1
+GOAT_PREC_BF16 = 0
+GOAT_PREC_FP32 = 1
+GOAT_TRACE_MAX = 256
+
+EXPORTED = ["goat_default_params", "goat_strerror", "goat_workspace_bytes", "goat_match", "goat_match_host",
+            "goat_gradient", "goat_sinkhorn", "goat_line_search", "goat_fw_update", "goat_project",
+            "goat_objective", "goat_gemm_bf16_xyT"]
+
+
+class GoatError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} ({status})")
+
+
+class goat_params(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("sk_max_iter", ctypes.c_int), ("sk_tol", ctypes.c_float),
+                ("sk_warm_start", ctypes.c_int), ("sk_check_every", ctypes.c_int),
+                ("project_on_grad", ctypes.c_int), ("lap_max_rounds", ctypes.c_int)]
+
+
+class goat_stats(ctypes.Structure):
+    _fields_ = [("fw_iters", ctypes.c_int), ("converged", ctypes.c_int), ("sk_iters_total", ctypes.c_int),
+                ("sk_iters", ctypes.c_int * GOAT_TRACE_MAX), ("sk_resid", ctypes.c_float * GOAT_TRACE_MAX),
+                ("alpha", ctypes.c_double * GOAT_TRACE_MAX), ("objective", ctypes.c_double),
+                ("disagreements", ctypes.c_double), ("lap_gap", ctypes.c_double), ("lap_rounds", ctypes.c_int),
+                ("ms_total", ctypes.c_float), ("ms_fw", ctypes.c_float), ("ms_project", ctypes.c_float)]
+
+
+_lock = threading.Lock()
+_lib = None
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_f = ctypes.c_float
+_d = ctypes.c_double
+
+
+def load():
+    """Loads libgoat.so (built by ``paper_2111_05366_gb300._build``); raises if it is absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgoat.so not found at {LIB_PATH}; build it with "
+                               "`python -m paper_2111_05366_gb300._build` (no CPU fallback exists)")
+        lib = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "goat_default_params": (None, [ctypes.POINTER(goat_params)]),
+            "goat_strerror": (ctypes.c_char_p, [_i]),
+            "goat_workspace_bytes": (ctypes.c_size_t, [_i, _i, _i]),
+            "goat_match": (_i, [_vp, _vp, _i, _i, _vp, _f, _i, _f, ctypes.POINTER(goat_params), _vp,
+                                ctypes.POINTER(_d), ctypes.POINTER(goat_stats), _vp, ctypes.c_size_t, _vp]),
+            "goat_match_host": (_i, [_vp, _vp, _i, _i, _vp, _f, _i, _f, ctypes.POINTER(goat_params), _vp,
+                                     ctypes.POINTER(_d), ctypes.POINTER(goat_stats), _vp, ctypes.c_size_t, _vp]),
+            "goat_gradient": (_i, [_vp, _vp, _i, _i, _vp, _vp, _i, _vp, ctypes.c_size_t, _vp]),
+            "goat_sinkhorn": (_i, [_vp, _i, _f, _f, _i, _vp, _vp, _vp, ctypes.POINTER(_i), ctypes.POINTER(_f), _vp,
+                                   ctypes.c_size_t, _vp]),
+            "goat_line_search": (_i, [_vp, _vp, _vp, _vp, _i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d),
+                                      ctypes.POINTER(_d), _vp, ctypes.c_size_t, _vp]),
+            "goat_fw_update": (_i, [_vp, _vp, _vp, _vp, _i, _d, _vp]),
+            "goat_project": (_i, [_vp, _i, _i, _vp, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp, ctypes.c_size_t,
+                                  _vp]),
+            "goat_objective": (_i, [_vp, _vp, _i, _i, _vp, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp,
+                                    ctypes.c_size_t, _vp]),
+            "goat_gemm_bf16_xyT": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _i, _f, _vp, _i, _i, _i, _vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def strerror(status: int) -> str:
+    return load().goat_strerror(int(status)).decode()
+
+
+def _check(status: int, where: str, allow=(GOAT_OK,)):
+    if status not in allow:
+        raise GoatError(status, where)
+    return status
+
+
+# ---------------------------------------------------------------- marshalling
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, dtype=None, shape=None, name="tensor"):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _adj_dtype(A):
+    torch = _torch()
+    if A.dtype == torch.uint8:
+        return GOAT_DTYPE_U8
+    if A.dtype == torch.float32:
+        return GOAT_DTYPE_F32
+    raise TypeError("adjacency matrices must be uint8 (0/1) or float32")
+
+
+def default_params(**overrides) -> goat_params:
+    p = goat_params()
+    load().goat_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def workspace_bytes(n: int, dtype_AB: int = GOAT_DTYPE_U8, precision: int = GOAT_PREC_BF16) -> int:
+    return int(load().goat_workspace_bytes(int(n), int(dtype_AB), int(precision)))
+
+
+def _stats_dict(st: goat_stats) -> dict:
+    k = min(st.fw_iters, GOAT_TRACE_MAX)
+    return {"fw_iters": st.fw_iters, "converged": bool(st.converged), "sk_iters_total": st.sk_iters_total,
+            "sk_iters": list(st.sk_iters[:k]), "sk_resid": list(st.sk_resid[:k]), "alpha": list(st.alpha[:k]),
+            "objective": st.objective, "disagreements": st.disagreements, "lap_gap": st.lap_gap,
+            "lap_rounds": st.lap_rounds, "ms_total": st.ms_total, "ms_fw": st.ms_fw, "ms_project": st.ms_project}
+
+
+# ---------------------------------------------------------------- entry points
+
+def goat_match(A, B, init=None, eps_rel: float = 0.03, max_iter: int = 30, tol: float = 0.03,
+               params: goat_params | None = None, workspace=None):
+    """Whole GOAT solve (Alg. 3) on device tensors A, B (n x n, uint8 or float32).
+
+    Returns (perm int32 numpy [n], objective, stats dict)."""
+    n = A.shape[0]
+    dt = _adj_dtype(A)
+    a = _dev(A, A.dtype, (n, n), "A")
+    b = _dev(B, A.dtype, (n, n), "B")
+    ini = _dev(init, _torch().float32, (n, n), "init") if init is not None else None
+    perm = np.empty(n, dtype=np.int32)
+    obj = ctypes.c_double()
+    st = goat_stats()
+    p = params if params is not None else default_params()
+    ws = _dev(workspace, None, None, "workspace") if workspace is not None else None
+    wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    r = load().goat_match(a, b, n, dt, ini, float(eps_rel), int(max_iter), float(tol), ctypes.byref(p),
+                          perm.ctypes.data_as(ctypes.c_void_p), ctypes.byref(obj), ctypes.byref(st), ws, wsb,
+                          _stream())
+    _check(r, "goat_match")
+    return perm, obj.value, _stats_dict(st)
+
+
+def goat_match_host(A, B, init=None, eps_rel: float = 0.03, max_iter: int = 30, tol: float = 0.03,
+                    params: goat_params | None = None, workspace=None):
+    """GOAT solve from HOST numpy arrays (the copies to the device are part of the call)."""
+    A = np.ascontiguousarray(A)
+    B = np.ascontiguousarray(B)
+    if A.dtype == np.uint8:
+        dt = GOAT_DTYPE_U8
+    elif A.dtype == np.float32:
+        dt = GOAT_DTYPE_F32
+    else:
+        raise TypeError("A must be uint8 or float32")
+    if B.dtype != A.dtype or A.shape != B.shape or A.ndim != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("A and B must be square arrays of the same shape and dtype")
+    n = A.shape[0]
+    ini = np.ascontiguousarray(init, dtype=np.float32) if init is not None else None
+    perm = np.empty(n, dtype=np.int32)
+    obj = ctypes.c_double()
+    st = goat_stats()
+    p = params if params is not None else default_params()
+    ws = _dev(workspace, None, None, "workspace") if workspace is not None else None
+    wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    r = load().goat_match_host(A.ctypes.data_as(ctypes.c_void_p), B.ctypes.data_as(ctypes.c_void_p), n, dt,
+                               ini.ctypes.data_as(ctypes.c_void_p) if ini is not None else None, float(eps_rel),
+                               int(max_iter), float(tol), ctypes.byref(p), perm.ctypes.data_as(ctypes.c_void_p),
+                               ctypes.byref(obj), ctypes.byref(st), ws, wsb, _stream())
+    _check(r, "goat_match_host")
+    return perm, obj.value, _stats_dict(st)
+
+
+def goat_gradient(A, B, P, precision: int = GOAT_PREC_BF16, out=None):
+    """G = -grad f(P) = -2 A P B (Alg. 3 step 1) on the tensor cores; returns a float32 tensor."""
+    torch = _torch()
+    n = A.shape[0]
+    G = out if out is not None else torch.empty((n, n), dtype=torch.float32, device=A.device)
+    r = load().goat_gradient(_dev(A, A.dtype, (n, n), "A"), _dev(B, A.dtype, (n, n), "B"), n, _adj_dtype(A),
+                             _dev(P, torch.float32, (n, n), "P"), _dev(G, torch.float32, (n, n), "G"),
+                             int(precision), None, 0, _stream())
+    _check(r, "goat_gradient")
+    return G
+
+
+def goat_sinkhorn(G, eps: float, tol: float, max_iter: int, g_init=None, want_Q: bool = False):
+    """LOT (Alg. 2): log-domain Sinkhorn on exp(-G/eps).  Returns (f, g, Q or None, iters, resid)."""
+    torch = _torch()
+    n = G.shape[0]
+    f = torch.empty(n, dtype=torch.float32, device=G.device)
+    g = (g_init.clone() if g_init is not None else torch.zeros(n, dtype=torch.float32, device=G.device))
+    Q = torch.empty((n, n), dtype=torch.float32, device=G.device) if want_Q else None
+    it = ctypes.c_int()
+    res = ctypes.c_float()
+    r = load().goat_sinkhorn(_dev(G, torch.float32, (n, n), "G"), n, float(eps), float(tol), int(max_iter),
+                             _dev(f, torch.float32, (n,), "f"), _dev(g, torch.float32, (n,), "g"),
+                             _dev(Q, torch.float32, (n, n), "Q") if Q is not None else None, ctypes.byref(it),
+                             ctypes.byref(res), None, 0, _stream())
+    _check(r, "goat_sinkhorn")
+    return f, g, Q, it.value, res.value
+
+
+def goat_line_search(G, G_Q, P, Q, maximize: bool = True):
+    """Exact quadratic step (Alg. 3 step 3).  Returns (alpha, a, b); alpha weights Q."""
+    torch = _torch()
+    n = G.shape[0]
+    al, a, b = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    sh = (n, n)
+    r = load().goat_line_search(_dev(G, torch.float32, sh, "G"), _dev(G_Q, torch.float32, sh, "G_Q"),
+                                _dev(P, torch.float32, sh, "P"), _dev(Q, torch.float32, sh, "Q"), n,
+                                int(bool(maximize)), ctypes.byref(al), ctypes.byref(a), ctypes.byref(b), None, 0,
+                                _stream())
+    _check(r, "goat_line_search")
+    return al.value, a.value, b.value
+
+
+def goat_fw_update(P, G, Q, G_Q, alpha: float):
+    """In place: P += alpha (Q - P), G += alpha (G_Q - G) (Alg. 3 step 4)."""
+    torch = _torch()
+    n = P.shape[0]
+    sh = (n, n)
+    r = load().goat_fw_update(_dev(P, torch.float32, sh, "P"), _dev(G, torch.float32, sh, "G"),
+                              _dev(Q, torch.float32, sh, "Q"), _dev(G_Q, torch.float32, sh, "G_Q"), n, float(alpha),
+                              _stream())
+    _check(r, "goat_fw_update")
+
+
+def goat_project(M, maximize: bool = True, allow_uncertified: bool = False):
+    """Linear assignment on the GPU (auction + LP-duality certification).
+
+    Returns (perm int32 tensor, cost, gap) with cost = sum_i M[i, perm i] in FP64."""
+    torch = _torch()
+    n = M.shape[0]
+    perm = torch.empty(n, dtype=torch.int32, device=M.device)
+    cost, gap = ctypes.c_double(), ctypes.c_double()
+    r = load().goat_project(_dev(M, torch.float32, (n, n), "M"), n, int(bool(maximize)),
+                            _dev(perm, torch.int32, (n,), "perm"), ctypes.byref(cost), ctypes.byref(gap), None, 0,
+                            _stream())
+    allow = (GOAT_OK, GOAT_ERR_NOT_CONVERGED) if allow_uncertified else (GOAT_OK,)
+    _check(r, "goat_project", allow)
+    return perm, cost.value, gap.value
+
+
+def goat_objective(A, B, perm):
+    """f(perm) = sum_ij A_ij B[perm i, perm j] and the disagreement count (exact for uint8)."""
+    torch = _torch()
+    n = A.shape[0]
+    obj, dis = ctypes.c_double(), ctypes.c_double()
+    r = load().goat_objective(_dev(A, A.dtype, (n, n), "A"), _dev(B, A.dtype, (n, n), "B"), n, _adj_dtype(A),
+                              _dev(perm, torch.int32, (n,), "perm"), ctypes.byref(obj), ctypes.byref(dis), None, 0,
+                              _stream())
+    _check(r, "goat_objective")
+    return obj.value, dis.value
+
+
+def goat_gemm_bf16_xyT(X, Y, k_total: int, kx_period: int, scale: float = 1.0, out_rows=None, out_cols=None):
+    """out = scale * X[:, k mod kx_period] Y[:, k]^T on the tensor cores (kernel-level entry)."""
+    torch = _torch()
+    xr, xs = X.shape
+    yr, ys = Y.shape
+    orows = xr if out_rows is None else out_rows
+    ocols = yr if out_cols is None else out_cols
+    out = torch.empty((orows, ocols), dtype=torch.float32, device=X.device)
+    r = load().goat_gemm_bf16_xyT(_dev(X, torch.bfloat16, None, "X"), xr, xs, int(kx_period),
+                                  _dev(Y, torch.bfloat16, None, "Y"), yr, ys, int(k_total), float(scale),
+                                  _dev(out, torch.float32, None, "out"), ocols, orows, ocols, _stream())
+    _check(r, "goat_gemm_bf16_xyT")
+    return out

@@ -1,0 +1,465 @@
+// goat_fw.cu -- the memory-bound kernels of the Frank-Wolfe loop (Alg. 3):
+// operand preparation, the closed-form first gradient, the line-search
+// reductions (K3), the update (K4) and the objective at a permutation.
+#include <algorithm>
+
+#include "goat_common.cuh"
+#include "goat_internal.h"
+
+namespace goat {
+
+// ---------------------------------------------------------------- operands
+
+// Adjacency (uint8 or float32, dense ld n) -> BF16 GEMM operand (row stride ld16,
+// zero padding), plus row sums (degrees) in FP32.  One warp per row.
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_to_bf16(const T *__restrict__ A, int n, __nv_bfloat16 *__restrict__ A16,
+                                                     int ld16, float *__restrict__ deg) {
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb) {
+        const T *src = A + (long long)i * n;
+        __nv_bfloat16 *dst = A16 + (long long)i * ld16;
+        float s = 0.0f;
+        for (int j = lane; j < ld16; j += 32) {
+            const float v = (j < n) ? (float)src[j] : 0.0f;
+            dst[j] = __float2bfloat16_rn(v);
+            s += v;
+        }
+        s = warp_sum(s);
+        if (lane == 0 && deg) deg[i] = s;
+    }
+}
+
+// Counts pairs with A[i][j] != A[j][i] (32 x 32 tiles through shared memory).
+template <typename T>
+__global__ void k_count_asym(const T *__restrict__ A, int n, int *__restrict__ count) {
+    __shared__ float tile[32][33];
+    const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
+    if (bj < bi) return;  // each unordered tile pair once
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        const int i = bj + r, j = bi + tx;
+        tile[r][tx] = (i < n && j < n) ? (float)A[(long long)i * n + j] : 0.0f;
+    }
+    __syncthreads();
+    int bad = 0;
+    for (int r = ty; r < 32; r += 8) {
+        const int i = bi + r, j = bj + tx;
+        if (i < n && j < n) {
+            const float a = (float)A[(long long)i * n + j];
+            if (a != tile[tx][r]) ++bad;
+            if (i == j && a != 0.0f) ++bad;  // diagonal must be zero
+        }
+    }
+    if (bad) atomicAdd(count, bad);
+}
+
+// FP32 matrix (ld n) -> BF16 split terms (hi [, lo]) with row stride terms*ld16.
+__global__ void __launch_bounds__(256) k_f32_to_terms(const float *__restrict__ X, int n, long long ldx,
+                                                      __nv_bfloat16 *__restrict__ Xb, int ld16, int terms) {
+    const int chunks = ld16 / 8;
+    const long long total = (long long)n * chunks;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / chunks);
+        const int j0 = (int)(t - (long long)i * chunks) * 8;
+        float q[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) q[k] = (j0 + k < n) ? X[(long long)i * ldx + j0 + k] : 0.0f;
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(q[k], q[k + 1]);
+            const float2 hf = __bfloat1622float2(h2);
+            const __nv_bfloat162 l2 = __floats2bfloat162_rn(q[k] - hf.x, q[k + 1] - hf.y);
+            hw[k / 2] = *reinterpret_cast<const uint32_t *>(&h2);
+            lw[k / 2] = *reinterpret_cast<const uint32_t *>(&l2);
+        }
+        __nv_bfloat16 *row = Xb + (long long)i * ((long long)terms * ld16);
+        *reinterpret_cast<uint4 *>(row + j0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        if (terms > 1) *reinterpret_cast<uint4 *>(row + ld16 + j0) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+}
+
+// ---------------------------------------------------------------- first gradient
+
+// At the barycenter J = 11^T/n:  grad f(J) = (A 1)(B 1)^T / n + (A^T 1)(B^T 1)^T / n,
+// i.e. G = -(2/n) d_A d_B^T for symmetric graphs.  Also fills P = J and records max|G|.
+__global__ void __launch_bounds__(256) k_barycenter(const float *__restrict__ dA, const float *__restrict__ dB, int n,
+                                                    float *__restrict__ G, float *__restrict__ P, DevState *st) {
+    const float inv_n = 1.0f / (float)n;
+    const float scale = -2.0f * inv_n;
+    float gm = 0.0f;
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const float ai = scale * dA[i];
+        float *Gi = G + (long long)i * n;
+        float *Pi = P ? P + (long long)i * n : nullptr;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const float v = ai * dB[j];
+            Gi[j] = v;
+            if (Pi) Pi[j] = inv_n;
+            gm = fmaxf(gm, fabsf(v));
+        }
+    }
+    gm = warp_max(gm);
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&st->gmax_bits, gm);
+}
+
+__global__ void __launch_bounds__(256) k_absmax(const float *__restrict__ X, long long total, unsigned *out) {
+    float gm = 0.0f;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x)
+        gm = fmaxf(gm, fabsf(X[t]));
+    gm = warp_max(gm);
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, gm);
+}
+
+// ---------------------------------------------------------------- line search (K3)
+
+// Q value at (row i, column j) from the BF16 split terms the GEMMs consumed.
+__device__ __forceinline__ float q_terms(const __nv_bfloat16 *row, int ldq, int terms, int j) {
+    float q = __bfloat162float(row[j]);
+    if (terms > 1) q += __bfloat162float(row[ldq + j]);
+    return q;
+}
+
+// Per-block partial sums of <G, D>, <G_Q, D>, <D, D> with D = Q - P, where Q is
+// given either as BF16 split terms (the exact values the GEMMs consumed) or as
+// FP32.  One block per row at a time; FP32 within a row segment, FP64 across.
+__global__ void __launch_bounds__(256) k_ls_partial(const float *__restrict__ G, const float *__restrict__ GQ,
+                                                    const float *__restrict__ P, const __nv_bfloat16 *__restrict__ Qb,
+                                                    int ldq, int terms, const float *__restrict__ Qf, int n,
+                                                    double *__restrict__ out) {
+    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    const bool vec = ((n & 3) == 0) && (Qf == nullptr) &&
+                     (((reinterpret_cast<uintptr_t>(G) | reinterpret_cast<uintptr_t>(GQ) |
+                        reinterpret_cast<uintptr_t>(P)) & 15) == 0);
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const long long base = (long long)i * n;
+        const __nv_bfloat16 *qrow = Qb ? Qb + (long long)i * ((long long)terms * ldq) : nullptr;
+        float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        if (vec) {
+            for (int j = threadIdx.x * 4; j < n; j += blockDim.x * 4) {
+                const float4 g4 = *reinterpret_cast<const float4 *>(G + base + j);
+                const float4 h4 = *reinterpret_cast<const float4 *>(GQ + base + j);
+                const float4 p4 = *reinterpret_cast<const float4 *>(P + base + j);
+                const uint2 qh = *reinterpret_cast<const uint2 *>(qrow + j);
+                float q[4];
+                {
+                    const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&qh.x));
+                    const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&qh.y));
+                    q[0] = lo.x; q[1] = lo.y; q[2] = hi.x; q[3] = hi.y;
+                }
+                if (terms > 1) {
+                    const uint2 ql = *reinterpret_cast<const uint2 *>(qrow + ldq + j);
+                    const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&ql.x));
+                    const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&ql.y));
+                    q[0] += lo.x; q[1] += lo.y; q[2] += hi.x; q[3] += hi.y;
+                }
+                const float d0 = q[0] - p4.x, d1 = q[1] - p4.y, d2 = q[2] - p4.z, d3 = q[3] - p4.w;
+                a1 += g4.x * d0 + g4.y * d1 + g4.z * d2 + g4.w * d3;
+                a2 += h4.x * d0 + h4.y * d1 + h4.z * d2 + h4.w * d3;
+                a3 += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+            }
+        } else {
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                const float q = Qf ? Qf[base + j] : q_terms(qrow, ldq, terms, j);
+                const float d = q - P[base + j];
+                a1 = fmaf(G[base + j], d, a1);
+                a2 = fmaf(GQ[base + j], d, a2);
+                a3 = fmaf(d, d, a3);
+            }
+        }
+        s1 += a1;
+        s2 += a2;
+        s3 += a3;
+    }
+    s1 = warp_sum_d(s1);
+    s2 = warp_sum_d(s2);
+    s3 = warp_sum_d(s3);
+    __shared__ double red[3][8];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[0][w] = s1;
+        red[1][w] = s2;
+        red[2][w] = s3;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r1 = 0, r2 = 0, r3 = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            r1 += red[0][k];
+            r2 += red[1][k];
+            r3 += red[2][k];
+        }
+        out[3 * blockIdx.x + 0] = r1;
+        out[3 * blockIdx.x + 1] = r2;
+        out[3 * blockIdx.x + 2] = r3;
+    }
+}
+
+// Sums the partials in a fixed order and solves the 1-D quadratic.
+// b = -<G, D>, a = (1/2)(<G, D> - <G_Q, D>); alpha = argmax (maximize) over [0,1]
+// of b t + a t^2.  Also applies the Frank-Wolfe stop test ||alpha D||_F / sqrt(n) < tol
+// and records the trace.
+__global__ void k_ls_final(const double *__restrict__ part, int nblocks, int n, DevState *st) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s1 = 0, s2 = 0, s3 = 0;
+    for (int k = 0; k < nblocks; ++k) {
+        s1 += part[3 * k];
+        s2 += part[3 * k + 1];
+        s3 += part[3 * k + 2];
+    }
+    const double b = -s1, a = 0.5 * (s1 - s2);
+    double alpha;
+    if (st->maximize) {
+        if (a < 0.0) {
+            alpha = -b / (2.0 * a);
+            alpha = alpha < 0.0 ? 0.0 : (alpha > 1.0 ? 1.0 : alpha);
+        } else {
+            alpha = (a + b > 0.0) ? 1.0 : 0.0;
+        }
+    } else {
+        if (a > 0.0) {
+            alpha = -b / (2.0 * a);
+            alpha = alpha < 0.0 ? 0.0 : (alpha > 1.0 ? 1.0 : alpha);
+        } else {
+            alpha = (a + b < 0.0) ? 1.0 : 0.0;
+        }
+    }
+    if (!(alpha == alpha)) {
+        alpha = 0.0;
+        if (!st->error) st->error = GOAT_ERR_NAN;
+    }
+    st->ls_a = a;
+    st->ls_b = b;
+    st->ls_dd = s3;
+    st->alpha = alpha;
+    const double change = alpha * sqrt(s3 > 0.0 ? s3 : 0.0) / sqrt((double)n);
+    const int it = st->fw_iter;
+    if (it < GOAT_TRACE_MAX) {
+        st->tr_alpha[it] = alpha;
+        st->tr_sk_iters[it] = st->sk_iters;
+        st->tr_sk_resid[it] = st->sk_resid;
+    }
+    st->fw_iter = it + 1;
+    if (change < (double)st->fw_tol) st->fw_done = 1;
+}
+
+// ---------------------------------------------------------------- update (K4)
+
+// P <- P + alpha (Q - P), G <- G + alpha (G_Q - G); accumulates max|G_new|.
+__global__ void __launch_bounds__(256) k_fw_update(float *__restrict__ P, float *__restrict__ G,
+                                                   const float *__restrict__ GQ, const __nv_bfloat16 *__restrict__ Qb,
+                                                   int ldq, int terms, const float *__restrict__ Qf, int n,
+                                                   const DevState *__restrict__ st, float alpha_value,
+                                                   unsigned *gmax_out) {
+    const float alpha = st ? (float)st->alpha : alpha_value;
+    float gm = 0.0f;
+    const bool vec = ((n & 3) == 0) && (Qf == nullptr) &&
+                     (((reinterpret_cast<uintptr_t>(G) | reinterpret_cast<uintptr_t>(GQ) |
+                        reinterpret_cast<uintptr_t>(P)) & 15) == 0);
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const long long base = (long long)i * n;
+        const __nv_bfloat16 *qrow = Qb ? Qb + (long long)i * ((long long)terms * ldq) : nullptr;
+        if (vec) {
+            for (int j = threadIdx.x * 4; j < n; j += blockDim.x * 4) {
+                float4 p4 = *reinterpret_cast<const float4 *>(P + base + j);
+                float4 g4 = *reinterpret_cast<const float4 *>(G + base + j);
+                const float4 h4 = *reinterpret_cast<const float4 *>(GQ + base + j);
+                const uint2 qh = *reinterpret_cast<const uint2 *>(qrow + j);
+                float q[4];
+                {
+                    const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&qh.x));
+                    const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&qh.y));
+                    q[0] = lo.x; q[1] = lo.y; q[2] = hi.x; q[3] = hi.y;
+                }
+                if (terms > 1) {
+                    const uint2 ql = *reinterpret_cast<const uint2 *>(qrow + ldq + j);
+                    const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&ql.x));
+                    const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&ql.y));
+                    q[0] += lo.x; q[1] += lo.y; q[2] += hi.x; q[3] += hi.y;
+                }
+                p4.x = fmaf(alpha, q[0] - p4.x, p4.x);
+                p4.y = fmaf(alpha, q[1] - p4.y, p4.y);
+                p4.z = fmaf(alpha, q[2] - p4.z, p4.z);
+                p4.w = fmaf(alpha, q[3] - p4.w, p4.w);
+                g4.x = fmaf(alpha, h4.x - g4.x, g4.x);
+                g4.y = fmaf(alpha, h4.y - g4.y, g4.y);
+                g4.z = fmaf(alpha, h4.z - g4.z, g4.z);
+                g4.w = fmaf(alpha, h4.w - g4.w, g4.w);
+                *reinterpret_cast<float4 *>(P + base + j) = p4;
+                *reinterpret_cast<float4 *>(G + base + j) = g4;
+                gm = fmaxf(gm, fmaxf(fmaxf(fabsf(g4.x), fabsf(g4.y)), fmaxf(fabsf(g4.z), fabsf(g4.w))));
+            }
+        } else {
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                const float q = Qf ? Qf[base + j] : q_terms(qrow, ldq, terms, j);
+                const float p = P[base + j], g = G[base + j];
+                P[base + j] = fmaf(alpha, q - p, p);
+                const float gn = fmaf(alpha, GQ[base + j] - g, g);
+                G[base + j] = gn;
+                gm = fmaxf(gm, fabsf(gn));
+            }
+        }
+    }
+    gm = warp_max(gm);
+    if (gmax_out && (threadIdx.x & 31) == 0) atomic_max_nonneg(gmax_out, gm);
+}
+
+// Moves the max|G| accumulated by the update into the current slot.
+__global__ void k_fw_roll(DevState *st) {
+    st->gmax_bits = st->gmax_next;
+    st->gmax_next = 0u;
+}
+
+// ---------------------------------------------------------------- objective
+
+// sum_ij A_ij B[perm i][perm j]; exact 64-bit integer sums for byte inputs,
+// FP64 for float inputs.  One block per row range.
+template <typename T>
+__global__ void __launch_bounds__(256) k_objective(const T *__restrict__ A, const T *__restrict__ B,
+                                                   const int32_t *__restrict__ perm, int n,
+                                                   unsigned long long *isum, double *fsum, int *bad_perm) {
+    long long acc_i = 0;
+    double acc_f = 0.0;
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const int pi = perm[i];
+        if (pi < 0 || pi >= n) {
+            if (threadIdx.x == 0) atomicAdd(bad_perm, 1);
+            continue;
+        }
+        const T *ai = A + (long long)i * n;
+        const T *bp = B + (long long)pi * n;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const T a = ai[j];
+            if (a != (T)0) {
+                const int pj = perm[j];
+                if (pj < 0 || pj >= n) continue;
+                const T b = bp[pj];
+                if (sizeof(T) == 1)
+                    acc_i += (long long)a * (long long)b;
+                else
+                    acc_f += (double)a * (double)b;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        acc_i += __shfl_xor_sync(0xffffffffu, acc_i, o);
+        acc_f += __shfl_xor_sync(0xffffffffu, acc_f, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (sizeof(T) == 1)
+            atomicAdd(isum, (unsigned long long)acc_i);
+        else
+            atomicAdd(fsum, acc_f);
+    }
+}
+
+// Sum of squared entries (||A||_F^2) for the disagreement count.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sqnorm(const T *__restrict__ A, long long total, unsigned long long *isum,
+                                                double *fsum) {
+    long long ai = 0;
+    double af = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const T a = A[t];
+        if (sizeof(T) == 1)
+            ai += (long long)a * a;
+        else
+            af += (double)a * (double)a;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        af += __shfl_xor_sync(0xffffffffu, af, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (sizeof(T) == 1)
+            atomicAdd(isum, (unsigned long long)ai);
+        else
+            atomicAdd(fsum, af);
+    }
+}
+
+// ---------------------------------------------------------------- host wrappers
+
+static int grid_for(long long work, int per_block = 256, int cap_per_sm = 16) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long g = ceil_div(work, per_block);
+    return (int)std::max<long long>(1, std::min<long long>(g, (long long)sms * cap_per_sm));
+}
+
+static int rows_grid(int n, int cap_per_sm = 8) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(1, std::min(n, sms * cap_per_sm));
+}
+
+int adj_to_bf16(const void *A, int dtype, int n, __nv_bfloat16 *A16, int ld16, float *deg, cudaStream_t s) {
+    const int grid = grid_for((long long)n * 32, 256, 16);
+    if (dtype == GOAT_DTYPE_U8)
+        k_adj_to_bf16<uint8_t><<<grid, 256, 0, s>>>((const uint8_t *)A, n, A16, ld16, deg);
+    else
+        k_adj_to_bf16<float><<<grid, 256, 0, s>>>((const float *)A, n, A16, ld16, deg);
+    return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
+}
+
+int count_asym(const void *A, int dtype, int n, int *count_dev, cudaStream_t s) {
+    dim3 grid((unsigned)ceil_div(n, 32), (unsigned)ceil_div(n, 32)), block(32, 8);
+    if (dtype == GOAT_DTYPE_U8)
+        k_count_asym<uint8_t><<<grid, block, 0, s>>>((const uint8_t *)A, n, count_dev);
+    else
+        k_count_asym<float><<<grid, block, 0, s>>>((const float *)A, n, count_dev);
+    return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
+}
+
+void f32_to_terms(const float *X, int n, long long ldx, __nv_bfloat16 *Xb, int ld16, int terms, cudaStream_t s) {
+    k_f32_to_terms<<<grid_for((long long)n * (ld16 / 8)), 256, 0, s>>>(X, n, ldx, Xb, ld16, terms);
+}
+
+void barycenter(const float *dA, const float *dB, int n, float *G, float *P, DevState *st, cudaStream_t s) {
+    k_barycenter<<<rows_grid(n), 256, 0, s>>>(dA, dB, n, G, P, st);
+}
+
+void absmax(const float *X, long long total, unsigned *out, cudaStream_t s) {
+    k_absmax<<<grid_for(total), 256, 0, s>>>(X, total, out);
+}
+
+int ls_blocks(int n) { return rows_grid(n, 4); }
+
+void line_search(const float *G, const float *GQ, const float *P, const __nv_bfloat16 *Qb, int ldq, int terms,
+                 const float *Qf, int n, double *partial, DevState *st, cudaStream_t s) {
+    const int nb = ls_blocks(n);
+    k_ls_partial<<<nb, 256, 0, s>>>(G, GQ, P, Qb, ldq, terms, Qf, n, partial);
+    k_ls_final<<<1, 32, 0, s>>>(partial, nb, n, st);
+}
+
+void fw_update(float *P, float *G, const float *GQ, const __nv_bfloat16 *Qb, int ldq, int terms, const float *Qf,
+               int n, const DevState *st, float alpha_value, unsigned *gmax_out, cudaStream_t s) {
+    k_fw_update<<<rows_grid(n), 256, 0, s>>>(P, G, GQ, Qb, ldq, terms, Qf, n, st, alpha_value, gmax_out);
+}
+
+void fw_roll(DevState *st, cudaStream_t s) { k_fw_roll<<<1, 1, 0, s>>>(st); }
+
+int objective(const void *A, const void *B, int dtype, int n, const int32_t *perm, unsigned long long *isum,
+              double *fsum, unsigned long long *nA, unsigned long long *nB, double *fA, double *fB, int *bad,
+              cudaStream_t s) {
+    const int grid = (int)std::min<long long>(n, 152LL * 8);
+    const long long total = (long long)n * n;
+    if (dtype == GOAT_DTYPE_U8) {
+        k_objective<uint8_t><<<grid, 256, 0, s>>>((const uint8_t *)A, (const uint8_t *)B, perm, n, isum, fsum, bad);
+        k_sqnorm<uint8_t><<<grid_for(total), 256, 0, s>>>((const uint8_t *)A, total, nA, fA);
+        k_sqnorm<uint8_t><<<grid_for(total), 256, 0, s>>>((const uint8_t *)B, total, nB, fB);
+    } else {
+        k_objective<float><<<grid, 256, 0, s>>>((const float *)A, (const float *)B, perm, n, isum, fsum, bad);
+        k_sqnorm<float><<<grid_for(total), 256, 0, s>>>((const float *)A, total, nA, fA);
+        k_sqnorm<float><<<grid_for(total), 256, 0, s>>>((const float *)B, total, nB, fB);
+    }
+    return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
+}
+
+}  // namespace goat

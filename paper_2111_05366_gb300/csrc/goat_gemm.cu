@@ -1,0 +1,381 @@
+// goat_gemm.cu -- K1: the two n x n x n products of the GOAT gradient on the
+// 5th-generation tensor cores (tcgen05 + TMEM), fed by TMA.
+//
+// Alg. 3 step 1 needs grad f(Q) = A Q B^T + A^T Q B, which for symmetric A, B is
+// 2 A Q B.  Both products are computed as "D = X Y^T" with X and Y row-major
+// (K contiguous), so every operand is K-major and is staged by TMA with the
+// 128-byte swizzle the MMA descriptors expect:
+//
+//   product 1:  C1 = B Q^T      (X = B, Y = Q)    C1[j][i] = (Q B)[i][j]  -> C1 = (Q B)^T
+//   product 2:  G_Q = -2 A C1^T (X = A, Y = C1)   G_Q[i][j] = -2 (A Q B)[i][j]
+//
+// A K-period on X lets one launch accumulate several split terms of Y
+// (Y = [Y_hi | Y_lo] along K, X re-read for each term): that is how the
+// FP32-accurate form adds A Q_hi B + A Q_lo B in one TMEM accumulator.
+//
+// Kernel structure (one persistent CTA per SM, 192 threads):
+//   warp 0      TMA producer: X tile 128x64 and Y tile 256x64 per stage, 4 stages
+//   warp 1      TMEM owner and MMA issuer: 4 x tcgen05.mma M=128 N=256 K=16 per stage
+//   warps 2-5   epilogue: tcgen05.ld 32 lanes x 32 columns, scale, convert, store
+// Two TMEM accumulators (2 x 256 columns) let the epilogue of tile t overlap
+// the MMAs of tile t+1.  Every wait is bounded (see mbar_wait_bounded).
+#include <cstdio>
+#include <mutex>
+
+#include "goat_common.cuh"
+#include "goat_internal.h"
+
+namespace goat {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr uint32_t TILE_X_BYTES = BM * BK * 2;
+constexpr uint32_t TILE_Y_BYTES = BN * BK * 2;
+constexpr uint32_t STAGE_BYTES = TILE_X_BYTES + TILE_Y_BYTES;
+constexpr uint32_t TMEM_COLS = 2 * BN;
+constexpr int GEMM_THREADS = 192;
+constexpr int GROUP_M = 16;
+constexpr size_t GEMM_SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+
+struct GemmParams {
+    int M, N;            // output rows (from X) and columns (from Y)
+    int kx_period;       // X is read at k mod kx_period (multiple of BK)
+    int num_kb;          // K extent / BK
+    int tiles_m, tiles_n;
+    float scale;
+    int mode;            // GEMM_OUT_F32 or GEMM_OUT_BF16_TERMS
+    float *out_f32;
+    long long ld_out;    // FP32 output leading dimension
+    __nv_bfloat16 *out_b16;
+    int out_terms;       // 1 or 2 (hi, lo) BF16 terms
+    long long term_stride;  // elements between the hi and lo term of a row
+    long long row_stride;   // elements between rows of the BF16 output
+    int out_rows, out_cols; // rows / columns actually written
+    int *err;
+};
+
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int &tm, int &tn) {
+    const int group = GROUP_M * tiles_n;
+    const int g = t / group;
+    const int first = g * GROUP_M;
+    const int gm = min(tiles_m - first, GROUP_M);
+    const int r = t - g * group;
+    tm = first + r % gm;
+    tn = r / gm;
+}
+
+__device__ __forceinline__ bool wait_timeout_ns(uint32_t bar, uint32_t parity, uint64_t ns) {
+    const uint64_t t0 = global_timer_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_timer_ns() - t0 > ns) return false;
+    return true;
+}
+
+__device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 h) { return *reinterpret_cast<uint32_t *>(&h); }
+
+// Writes one accumulator row segment (32 consecutive columns) held by this thread.
+// All indexing is static so the segment stays in registers.
+__device__ __forceinline__ void store_tile_row(const GemmParams &p, int row, int col0, const float (&v)[32]) {
+    if (row >= p.out_rows) return;
+    const float s = p.scale;
+    if (p.mode == GEMM_OUT_F32) {
+        float *dst = p.out_f32 + (long long)row * p.ld_out + col0;
+        const bool full = (col0 + 32 <= p.out_cols) && ((p.ld_out & 3) == 0);
+        if (full) {
+#pragma unroll
+            for (int c = 0; c < 32; c += 4)
+                *reinterpret_cast<float4 *>(dst + c) = make_float4(v[c] * s, v[c + 1] * s, v[c + 2] * s, v[c + 3] * s);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+                if (col0 + c < p.out_cols) dst[c] = v[c] * s;
+        }
+        return;
+    }
+    __nv_bfloat16 *hi = p.out_b16 + (long long)row * p.row_stride + col0;
+    __nv_bfloat16 *lo = hi + p.term_stride;
+    const bool two = p.out_terms > 1;
+    const bool full = (col0 + 32 <= p.out_cols) && ((p.row_stride & 7) == 0) && ((p.term_stride & 7) == 0);
+    uint32_t hw[16], lw[16];
+#pragma unroll
+    for (int c = 0; c < 32; c += 2) {
+        const float x0 = v[c] * s, x1 = v[c + 1] * s;
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+        const float2 hf = __bfloat1622float2(h2);
+        hw[c / 2] = bf16x2_bits(h2);
+        lw[c / 2] = bf16x2_bits(__floats2bfloat162_rn(x0 - hf.x, x1 - hf.y));
+    }
+    if (full) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4 *>(hi + 8 * q) = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+        if (two) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                *reinterpret_cast<uint4 *>(lo + 8 * q) =
+                    make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            if (col0 + c < p.out_cols) {
+                const uint32_t hb = hw[c / 2], lb = lw[c / 2];
+                const unsigned short h16 = (c & 1) ? (unsigned short)(hb >> 16) : (unsigned short)(hb & 0xFFFFu);
+                const unsigned short l16 = (c & 1) ? (unsigned short)(lb >> 16) : (unsigned short)(lb & 0xFFFFu);
+                hi[c] = __ushort_as_bfloat16(h16);
+                if (two) lo[c] = __ushort_as_bfloat16(l16);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+    k_gemm_xyT(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, const GemmParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * STAGE_BYTES);
+    // bars: [0,S) full, [S,2S) empty, 2S..2S+1 tmem full, 2S+2..2S+3 tmem empty, 2S+4 drain
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bar0 = smem_u32(bars);
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+    auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+    auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+    const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull_bar(b), 1);
+            mbar_init(tempty_bar(b), 128);
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0 && lane == 0) {
+        prefetch_tmap(&tmX);
+        prefetch_tmap(&tmY);
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int num_tiles = p.tiles_m * p.tiles_n;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t issued_mask = 0, issued_parity = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+                int tm, tn;
+                tile_coords(t, p.tiles_m, p.tiles_n, tm, tn);
+                for (int kb = 0; kb < p.num_kb; ++kb) {
+                    if (!mbar_wait_bounded(empty_bar(stage), phase ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sx = sbase + stage * STAGE_BYTES;
+                    const int kk = kb * BK;
+                    mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
+                    tma_load_2d(sx, &tmX, full_bar(stage), kk % p.kx_period, tm * BM);
+                    tma_load_2d(sx + TILE_X_BYTES, &tmY, full_bar(stage), kk, tn * BN);
+                    issued_mask |= 1u << stage;
+                    issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                // let every copy in flight land before the CTA releases its shared memory
+                for (int s = 0; s < STAGES; ++s)
+                    if (issued_mask & (1u << s)) wait_timeout_ns(full_bar(s), (issued_parity >> s) & 1u, 200000000ull);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        const uint32_t idesc = idesc_bf16_f32(BM, BN);
+        int stage = 0;
+        uint32_t phase = 0;
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+            int w = (lane == 0) ? (int)mbar_wait_bounded(tempty_bar(acc), acc_phase ^ 1u, abort_flag) : 1;
+            if (!__shfl_sync(0xffffffffu, w, 0)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+            for (int kb = 0; kb < p.num_kb; ++kb) {
+                w = (lane == 0) ? (int)mbar_wait_bounded(full_bar(stage), phase, abort_flag) : 1;
+                if (!__shfl_sync(0xffffffffu, w, 0)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                if (lane == 0) {
+                    const uint32_t sx = sbase + stage * STAGE_BYTES;
+                    const uint32_t sy = sx + TILE_X_BYTES;
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k) {
+                        umma_bf16(d_tmem, smem_desc_sw128(sx + 32u * k), smem_desc_sw128(sy + 32u * k), idesc,
+                                  (kb | k) != 0 ? 1u : 0u);
+                    }
+                    umma_commit(empty_bar(stage));
+                }
+                __syncwarp();
+                if (++stage == STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+            if (!ok) break;
+            if (lane == 0) umma_commit(tfull_bar(acc));
+            __syncwarp();
+            acc ^= 1;
+            if (acc == 0) acc_phase ^= 1u;
+        }
+        // every MMA issued by this warp has finished before TMEM is released
+        if (lane == 0) {
+            umma_commit(drain_bar);
+            if (!wait_timeout_ns(drain_bar, 0, 200000000ull)) *abort_flag = 1;
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------ epilogue (warps 2..5)
+        const int q = warp & 3;  // TMEM lane quarter this warp may address
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (int t = blockIdx.x; t < num_tiles; t += gridDim.x) {
+            int tm, tn;
+            tile_coords(t, p.tiles_m, p.tiles_n, tm, tn);
+            int w = (lane == 0) ? (int)mbar_wait_bounded(tfull_bar(acc), acc_phase, abort_flag) : 1;
+            if (!__shfl_sync(0xffffffffu, w, 0)) break;
+            tc_fence_after();
+            const int row = tm * BM + q * 32 + lane;
+            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                float v[32];
+                tmem_ld_32x32b_x32(taddr + 32u * c, v);
+                tmem_wait_ld();
+                if (c == BN / 32 - 1) {
+                    tc_fence_before();
+                    mbar_arrive(tempty_bar(acc));
+                }
+                store_tile_row(p, row, tn * BN + c * 32, v);
+            }
+            acc ^= 1;
+            if (acc == 0) acc_phase ^= 1u;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, TMEM_COLS);
+    }
+    if (threadIdx.x == 0 && *abort_flag) atomicCAS(p.err, 0, (int)GOAT_ERR_TIMEOUT);
+}
+
+// ---------------------------------------------------------------- host side
+
+typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                      const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                      CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                      CUtensorMapFloatOOBfill);
+
+static PFN_encodeTiled_t get_encode_fn() {
+    static PFN_encodeTiled_t fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_encodeTiled_t>(p);
+    });
+    return fn;
+}
+
+// 2-D BF16 tensor map: inner extent `inner` (elements), `rows` rows `stride` elements apart,
+// box 64 x box_rows with the 128-byte swizzle; out-of-range elements read as zero.
+static int make_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows, uint64_t stride,
+                    uint32_t box_rows) {
+    PFN_encodeTiled_t enc = get_encode_fn();
+    if (!enc) return GOAT_ERR_CUDA;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || ((stride * 2) & 15)) return GOAT_ERR_INVALID_ARG;
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {stride * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? GOAT_OK : GOAT_ERR_CUDA;
+}
+
+int gemm_xyT(const GemmCall &c, cudaStream_t stream) {
+    if (c.M < 1 || c.N < 1 || c.k_total < 1 || (c.k_total % BK) || (c.kx_period % BK) || c.kx_period < 1)
+        return GOAT_ERR_INVALID_ARG;
+    static int sm_count = 0;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+        attr_err = cudaFuncSetAttribute(k_gemm_xyT, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM_BYTES);
+    });
+    if (attr_err != cudaSuccess || sm_count <= 0) return GOAT_ERR_CUDA;
+
+    CUtensorMap mx, my;
+    int st = make_map(&mx, c.X, (uint64_t)c.kx_period, (uint64_t)c.x_rows, (uint64_t)c.x_stride, BM);
+    if (st) return st;
+    st = make_map(&my, c.Y, (uint64_t)c.k_total, (uint64_t)c.y_rows, (uint64_t)c.y_stride, BN);
+    if (st) return st;
+
+    GemmParams p;
+    p.M = c.M;
+    p.N = c.N;
+    p.kx_period = c.kx_period;
+    p.num_kb = c.k_total / BK;
+    p.tiles_m = (int)ceil_div(c.M, BM);
+    p.tiles_n = (int)ceil_div(c.N, BN);
+    p.scale = c.scale;
+    p.mode = c.mode;
+    p.out_f32 = c.out_f32;
+    p.ld_out = c.ld_out;
+    p.out_b16 = c.out_b16;
+    p.out_terms = c.out_terms;
+    p.term_stride = c.term_stride;
+    p.row_stride = c.row_stride;
+    p.out_rows = c.out_rows;
+    p.out_cols = c.out_cols;
+    p.err = c.err;
+    const int tiles = p.tiles_m * p.tiles_n;
+    const int grid = tiles < sm_count ? tiles : sm_count;
+    k_gemm_xyT<<<grid, GEMM_THREADS, GEMM_SMEM_BYTES, stream>>>(mx, my, p);
+    return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
+}
+
+}  // namespace goat

@@ -1,0 +1,94 @@
+// goat_internal.h -- declarations shared by the translation units of libgoat.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/goat.h"
+
+namespace goat {
+
+enum { GEMM_OUT_F32 = 0, GEMM_OUT_BF16_TERMS = 1 };
+
+// One "D = scale * X Y^T" launch (see goat_gemm.cu).  X: x_rows rows, row
+// stride x_stride, read at k mod kx_period; Y: y_rows rows, row stride
+// y_stride, K extent k_total.  Both BF16, 16-byte aligned, K-major.
+struct GemmCall {
+    const __nv_bfloat16 *X;
+    int x_rows;
+    long long x_stride;
+    int kx_period;
+    const __nv_bfloat16 *Y;
+    int y_rows;
+    long long y_stride;
+    int k_total;
+    int M, N;
+    float scale;
+    int mode;
+    float *out_f32;
+    long long ld_out;
+    __nv_bfloat16 *out_b16;
+    int out_terms;
+    long long term_stride;
+    long long row_stride;
+    int out_rows, out_cols;
+    int *err;
+};
+
+int gemm_xyT(const GemmCall &c, cudaStream_t stream);
+
+// Byte layout of the scratch workspace for size n (all offsets 256-aligned).
+struct Workspace {
+    size_t state;       // DevState
+    size_t A16, B16;    // BF16 adjacency, n rows x ld
+    size_t Xq;          // BF16 split terms of the right operand (Q or P), n rows x (terms*ld)
+    size_t C1;          // BF16 split terms of (Q B)^T, n rows x (terms*ld)
+    size_t GQ;          // FP32 n x n  (-grad f(Q))
+    size_t P, G;        // FP32 n x n  (goat_match's own iterate and -gradient)
+    size_t Qf;          // FP32 n x n  scratch (unused by goat_match)
+    size_t f, g;        // FP32 duals
+    size_t deg;         // FP32 degrees of A and B (2n)
+    size_t partial;     // FP32 Sinkhorn column partial sums / FP64 reduction partials
+    size_t lap;         // auction scratch
+    size_t total;
+    int ld, terms;
+    long long partial_elems;
+};
+
+Workspace plan_workspace(int n, int dtype_AB, int precision, bool with_match_buffers);
+
+struct DevState;
+
+// goat_fw.cu
+int adj_to_bf16(const void *A, int dtype, int n, __nv_bfloat16 *A16, int ld16, float *deg, cudaStream_t s);
+int count_asym(const void *A, int dtype, int n, int *count_dev, cudaStream_t s);
+void f32_to_terms(const float *X, int n, long long ldx, __nv_bfloat16 *Xb, int ld16, int terms, cudaStream_t s);
+void barycenter(const float *dA, const float *dB, int n, float *G, float *P, DevState *st, cudaStream_t s);
+void absmax(const float *X, long long total, unsigned *out, cudaStream_t s);
+int ls_blocks(int n);
+void line_search(const float *G, const float *GQ, const float *P, const __nv_bfloat16 *Qb, int ldq, int terms,
+                 const float *Qf, int n, double *partial, DevState *st, cudaStream_t s);
+void fw_update(float *P, float *G, const float *GQ, const __nv_bfloat16 *Qb, int ldq, int terms, const float *Qf,
+               int n, const DevState *st, float alpha_value, unsigned *gmax_out, cudaStream_t s);
+void fw_roll(DevState *st, cudaStream_t s);
+int objective(const void *A, const void *B, int dtype, int n, const int32_t *perm, unsigned long long *isum,
+              double *fsum, unsigned long long *nA, unsigned long long *nB, double *fA, double *fB, int *bad,
+              cudaStream_t s);
+
+// goat_sinkhorn.cu
+long long sinkhorn_partial_elems(int n);
+void sinkhorn_begin(DevState *st, float eps, float tol, float *g_zero, int n, cudaStream_t s);
+int sinkhorn_solve(const float *G, int n, long long ld, float *f, float *g, double *partial, DevState *st,
+                   int max_iter, int check_every, int *host_flag, cudaStream_t s);
+void write_q(const float *G, int n, long long ld, const float *f, const float *g, const DevState *st,
+             __nv_bfloat16 *Qb, int ldq, int terms, float *Qf, long long ldf, cudaStream_t s);
+
+// goat_lap.cu
+int lap_chunks(int n);
+size_t lap_bytes(int n, int nchunks);
+int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_ws, DevState *st, int max_rounds,
+              double *cost_dev, int *host_pinned, double *gap_host, int *rounds_host, cudaStream_t s);
+
+}  // namespace goat

@@ -1,0 +1,334 @@
+// goat_sinkhorn.cu -- K2: LOT (Alg. 2) as log-domain Sinkhorn on exp(-G/eps),
+// with K = exp(-G/eps) never stored.
+//
+// Cuturi's Sinkhorn-Knopp scaling to the marginals 1_n (Sec. 3.3), written on
+// the duals: Q_ij = exp((f_i + g_j - G_ij)/eps).  One iteration:
+//   row scaling      f_i = -eps LSE_j((g_j - G_ij)/eps)                    (k_sk_row)
+//   column sums      S_j = sum_i exp((f_i + g_j - G_ij)/eps)               (k_sk_colpart + k_sk_colfinal)
+//   residual         max_j |S_j - 1|   (the column marginal error of the row-scaled Q)
+//   column scaling   g_j <- g_j - eps log S_j
+// The kernels work in base 2: with c = log2(e)/eps, exp((x)/eps) = 2^(c x).
+// After the row scaling every Q_ij <= 1, so the column sums need no max shift;
+// a column whose sum underflows (possible only far from convergence) is redone
+// with a max-stabilised log-sum-exp.  All kernels return at once when the
+// device-side stop flag is set, so the host can queue iterations ahead.
+#include <algorithm>
+
+#include "goat_common.cuh"
+#include "goat_internal.h"
+
+namespace goat {
+
+constexpr float kLog2e = 1.4426950408889634f;
+
+// ---------------------------------------------------------------- row scaling
+
+__device__ __forceinline__ void lse_push(float &m, float &s, float x) {
+    if (x > m) {
+        s = s * fast_exp2(m - x) + 1.0f;
+        m = x;
+    } else {
+        s += fast_exp2(x - m);
+    }
+}
+
+__device__ __forceinline__ void lse_merge(float &m, float &s, float m2, float s2) {
+    const float M = fmaxf(m, m2);
+    if (M == -INFINITY) {
+        m = M;
+        s = 0.0f;
+        return;
+    }
+    s = s * fast_exp2(m - M) + s2 * fast_exp2(m2 - M);
+    m = M;
+}
+
+// One warp per row.  Vector path (float4) when rows are 16-byte aligned.
+__global__ void __launch_bounds__(256) k_sk_row(const float *__restrict__ G, int n, long long ld,
+                                                const float *__restrict__ g, float *__restrict__ f,
+                                                const DevState *__restrict__ st) {
+    if (st->sk_done) return;
+    const float c = st->c;
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(G) & 15) == 0);
+    const int n4 = vec ? (n & ~3) : 0;
+    for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < n; row += gridDim.x * wpb) {
+        const float *Gi = G + (long long)row * ld;
+        float m = -INFINITY, s = 0.0f;
+        int j = lane * 4;
+        for (; j + 128 < n4; j += 256) {
+            const float4 a0 = __ldg(reinterpret_cast<const float4 *>(Gi + j));
+            const float4 a1 = __ldg(reinterpret_cast<const float4 *>(Gi + j + 128));
+            const float4 b0 = __ldg(reinterpret_cast<const float4 *>(g + j));
+            const float4 b1 = __ldg(reinterpret_cast<const float4 *>(g + j + 128));
+            const float x0 = (b0.x - a0.x) * c, x1 = (b0.y - a0.y) * c, x2 = (b0.z - a0.z) * c,
+                        x3 = (b0.w - a0.w) * c;
+            const float x4 = (b1.x - a1.x) * c, x5 = (b1.y - a1.y) * c, x6 = (b1.z - a1.z) * c,
+                        x7 = (b1.w - a1.w) * c;
+            const float mx = fmaxf(fmaxf(fmaxf(x0, x1), fmaxf(x2, x3)), fmaxf(fmaxf(x4, x5), fmaxf(x6, x7)));
+            if (mx > m) {
+                s *= fast_exp2(m - mx);
+                m = mx;
+            }
+            s += fast_exp2(x0 - m) + fast_exp2(x1 - m) + fast_exp2(x2 - m) + fast_exp2(x3 - m) +
+                 fast_exp2(x4 - m) + fast_exp2(x5 - m) + fast_exp2(x6 - m) + fast_exp2(x7 - m);
+        }
+        for (; j < n4; j += 128) {
+            const float4 a0 = __ldg(reinterpret_cast<const float4 *>(Gi + j));
+            const float4 b0 = __ldg(reinterpret_cast<const float4 *>(g + j));
+            lse_push(m, s, (b0.x - a0.x) * c);
+            lse_push(m, s, (b0.y - a0.y) * c);
+            lse_push(m, s, (b0.z - a0.z) * c);
+            lse_push(m, s, (b0.w - a0.w) * c);
+        }
+        for (int jj = n4 + lane; jj < n; jj += 32) lse_push(m, s, (__ldg(g + jj) - __ldg(Gi + jj)) * c);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float m2 = __shfl_xor_sync(0xffffffffu, m, o);
+            const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+            lse_merge(m, s, m2, s2);
+        }
+        if (lane == 0) f[row] = -(m + __log2f(s)) / c;
+    }
+}
+
+// ---------------------------------------------------------------- column sums
+
+// Partial column sums over a chunk of rows; each thread owns 4 adjacent columns.
+// Terms are summed in FP32 in groups of 16 rows and the groups in FP64.
+__global__ void __launch_bounds__(256) k_sk_colpart(const float *__restrict__ G, int n, long long ld,
+                                                    const float *__restrict__ f, const float *__restrict__ g,
+                                                    double *__restrict__ partial, int rows_per_chunk,
+                                                    const DevState *__restrict__ st) {
+    if (st->sk_done) return;
+    const float c = st->c;
+    const int j0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const int r0 = blockIdx.y * rows_per_chunk;
+    const int r1 = min(n, r0 + rows_per_chunk);
+    if (j0 >= n) return;
+    const bool vec = (j0 + 3 < n) && ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(G) & 15) == 0);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    float gj[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) gj[k] = (j0 + k < n) ? __ldg(g + j0 + k) : 0.0f;
+    if (vec) {
+        int i = r0;
+        while (i < r1) {
+            const int ie = min(r1, i + 16);
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 4
+            for (; i < ie; ++i) {
+                const float4 a = __ldg(reinterpret_cast<const float4 *>(G + (long long)i * ld + j0));
+                const float fi = __ldg(f + i);
+                s0 += fast_exp2((fi + gj[0] - a.x) * c);
+                s1 += fast_exp2((fi + gj[1] - a.y) * c);
+                s2 += fast_exp2((fi + gj[2] - a.z) * c);
+                s3 += fast_exp2((fi + gj[3] - a.w) * c);
+            }
+            acc[0] += s0;
+            acc[1] += s1;
+            acc[2] += s2;
+            acc[3] += s3;
+        }
+    } else {
+        for (int i = r0; i < r1; ++i) {
+            const float fi = __ldg(f + i);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (j0 + k < n) acc[k] += fast_exp2((fi + gj[k] - __ldg(G + (long long)i * ld + j0 + k)) * c);
+        }
+    }
+    double *dst = partial + (long long)blockIdx.y * n + j0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (j0 + k < n) dst[k] = acc[k];
+}
+
+// Combines the chunk partials, takes the residual and applies the column scaling.
+__global__ void __launch_bounds__(256) k_sk_colfinal(const double *__restrict__ partial, int nchunks, int n,
+                                                     const float *__restrict__ G, long long ld,
+                                                     const float *__restrict__ f, float *__restrict__ g,
+                                                     DevState *__restrict__ st) {
+    if (st->sk_done) return;
+    const float c = st->c;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    float r = 0.0f;
+    if (j < n) {
+        double S = 0.0;
+        for (int k = 0; k < nchunks; ++k) S += partial[(long long)k * n + j];
+        const float gj = g[j];
+        if (S > 1e-30 && S < 1e30) {
+            g[j] = gj - (float)(log2(S)) / c;
+            r = (float)fabs(S - 1.0);
+        } else {
+            // stabilised: g_j = -eps LSE_i((f_i - G_ij)/eps), S_j = 2^(c g_j_old) * sum
+            float m = -INFINITY, s = 0.0f;
+            for (int i = 0; i < n; ++i) lse_push(m, s, (f[i] - G[(long long)i * ld + j]) * c);
+            const double lS = (double)gj * c + m + log2((double)s);
+            g[j] = -(m + __log2f(s)) / c;
+            r = (float)fabs(exp2(lS) - 1.0);
+            if (!(r == r)) r = INFINITY;
+            atomicAdd(&st->sk_underflow, 1);
+        }
+    }
+    r = warp_max(r);
+    __shared__ float red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+        v = warp_max(v);
+        if (threadIdx.x == 0) atomic_max_nonneg(&st->resid_bits, v);
+    }
+}
+
+// Closes one iteration: records the residual, counts it, raises the stop flag.
+__global__ void k_sk_check(DevState *st, int max_iter) {
+    if (st->sk_done) return;
+    const float r = __uint_as_float(st->resid_bits);
+    st->resid_bits = 0u;
+    st->sk_resid = r;
+    st->sk_iters += 1;
+    if (!(r == r) || r == INFINITY) {
+        if (!st->error) st->error = GOAT_ERR_NAN;
+        st->sk_done = 1;
+    } else if (r < st->sk_tol || st->sk_iters >= max_iter) {
+        st->sk_done = 1;
+    }
+}
+
+// Resets the iteration state and the entropic weight for a new solve.
+// eps <= 0 means eps = eps_rel * max|G| (the Frank-Wolfe rule).
+__global__ void k_sk_begin(DevState *st, float eps, float tol, float *g_zero, int n) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        float e = eps;
+        if (!(e > 0.0f)) {
+            const float gm = __uint_as_float(st->gmax_bits);
+            e = st->eps_rel * gm;
+            if (!(e > 0.0f)) e = 1.0f;  // G == 0: every doubly stochastic Q is optimal
+        }
+        st->eps = e;
+        st->c = kLog2e / e;
+        st->sk_tol = tol;
+        st->sk_done = 0;
+        st->sk_iters = 0;
+        st->sk_resid = INFINITY;
+        st->resid_bits = 0u;
+    }
+    if (g_zero)
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) g_zero[j] = 0.0f;
+}
+
+// ---------------------------------------------------------------- Q materialisation
+
+// Q_ij = 2^(c (f_i + g_j - G_ij)), written as BF16 split terms (hi, and lo when
+// terms == 2) into the GEMM operand buffer, zero in the padding columns, and
+// optionally as FP32.
+__global__ void __launch_bounds__(256) k_write_q(const float *__restrict__ G, int n, long long ld,
+                                                 const float *__restrict__ f, const float *__restrict__ g,
+                                                 const DevState *__restrict__ st, __nv_bfloat16 *__restrict__ Qb,
+                                                 int ldq, int terms, float *__restrict__ Qf, long long ldf) {
+    const float c = st->c;
+    const int chunks = ldq / 8;  // 8 columns per thread
+    const long long total = (long long)n * chunks;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / chunks);
+        const int j0 = (int)(t - (long long)i * chunks) * 8;
+        const float fi = __ldg(f + i);
+        float q[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int j = j0 + k;
+            q[k] = (j < n) ? fast_exp2((fi + __ldg(g + j) - __ldg(G + (long long)i * ld + j)) * c) : 0.0f;
+        }
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(q[k], q[k + 1]);
+            const float2 hf = __bfloat1622float2(h2);
+            const __nv_bfloat162 l2 = __floats2bfloat162_rn(q[k] - hf.x, q[k + 1] - hf.y);
+            hw[k / 2] = *reinterpret_cast<const uint32_t *>(&h2);
+            lw[k / 2] = *reinterpret_cast<const uint32_t *>(&l2);
+        }
+        if (Qb) {
+            __nv_bfloat16 *row = Qb + (long long)i * ((long long)terms * ldq);
+            *reinterpret_cast<uint4 *>(row + j0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            if (terms > 1) *reinterpret_cast<uint4 *>(row + ldq + j0) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+        if (Qf) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (j0 + k < n) Qf[(long long)i * ldf + j0 + k] = q[k];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host driver
+
+struct SinkhornLaunch {
+    int row_grid, colpart_x, colpart_y, rows_per_chunk, final_grid;
+};
+
+static SinkhornLaunch sinkhorn_launch(int n) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    SinkhornLaunch L;
+    L.row_grid = (int)std::min<int64_t>(ceil_div(n, 8), (int64_t)sms * 16);
+    L.colpart_x = (int)ceil_div(n, 1024);
+    const int target = sms * 8;
+    int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(target, L.colpart_x), ceil_div(n, 64)));
+    L.rows_per_chunk = (int)ceil_div(n, chunks);
+    L.colpart_y = (int)ceil_div(n, L.rows_per_chunk);
+    L.final_grid = (int)ceil_div(n, 256);
+    return L;
+}
+
+long long sinkhorn_partial_elems(int n) {
+    SinkhornLaunch L = sinkhorn_launch(n);
+    return (long long)L.colpart_y * n;
+}
+
+// Queues one Sinkhorn iteration.
+static void sinkhorn_iteration(const float *G, int n, long long ld, float *f, float *g, double *partial,
+                               DevState *st, int max_iter, const SinkhornLaunch &L, cudaStream_t s) {
+    k_sk_row<<<L.row_grid, 256, 0, s>>>(G, n, ld, g, f, st);
+    k_sk_colpart<<<dim3(L.colpart_x, L.colpart_y), 256, 0, s>>>(G, n, ld, f, g, partial, L.rows_per_chunk, st);
+    k_sk_colfinal<<<L.final_grid, 256, 0, s>>>(partial, L.colpart_y, n, G, ld, f, g, st);
+    k_sk_check<<<1, 1, 0, s>>>(st, max_iter);
+}
+
+// Runs Sinkhorn until the device stop flag rises (tolerance or max_iter),
+// polling the flag every `check_every` iterations.  `host_flag` is pinned
+// host memory of at least 2 ints.  Returns a goat_status.
+int sinkhorn_solve(const float *G, int n, long long ld, float *f, float *g, double *partial, DevState *st,
+                   int max_iter, int check_every, int *host_flag, cudaStream_t s) {
+    const SinkhornLaunch L = sinkhorn_launch(n);
+    if (check_every < 1) check_every = 1;
+    int done_iters = 0;
+    while (done_iters < max_iter) {
+        const int k = std::min(check_every, max_iter - done_iters);
+        for (int t = 0; t < k; ++t) sinkhorn_iteration(G, n, ld, f, g, partial, st, max_iter, L, s);
+        done_iters += k;
+        if (cudaMemcpyAsync(host_flag, &st->sk_done, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return GOAT_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return GOAT_ERR_CUDA;
+        if (host_flag[0]) break;
+    }
+    return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
+}
+
+void sinkhorn_begin(DevState *st, float eps, float tol, float *g_zero, int n, cudaStream_t s) {
+    k_sk_begin<<<g_zero ? (int)std::min<int64_t>(ceil_div(n, 256), 1024) : 1, 256, 0, s>>>(st, eps, tol, g_zero, n);
+}
+
+void write_q(const float *G, int n, long long ld, const float *f, const float *g, const DevState *st,
+             __nv_bfloat16 *Qb, int ldq, int terms, float *Qf, long long ldf, cudaStream_t s) {
+    const long long total = (long long)n * (ldq / 8);
+    const int grid = (int)std::min<long long>(ceil_div(total, 256), 152LL * 32);
+    k_write_q<<<grid, 256, 0, s>>>(G, n, ld, f, g, st, Qb, ldq, terms, Qf, ldf);
+}
+
+}  // namespace goat

@@ -1,0 +1,308 @@
+"""GPU parity of every hot-path step against the FP64 CPU oracle, through the C ABI.
+
+Sizes span several GEMM tiles (128 x 256) with ragged tails; inputs are the
+seeded correlated graphs of ``synthetic``.  Tolerances:
+  gradient      relative Frobenius error <= 1e-5 (FP32 form), <= 2e-2 (BF16 form)
+  Sinkhorn      duals within 2e-3 eps, Q within 1e-3 relative (+1e-6 absolute),
+                marginals <= 1e-4 at convergence
+  line search   alpha, a, b within 1e-4 relative
+  projection    cost equal to the oracle Hungarian's: bitwise on integer
+                matrices, within n 2^-52 max|c| otherwise (FP64 sums of FP32 entries)
+  objective     exact integer
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_05366_gb300 import synthetic
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # collected on CPU hosts, skipped there
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2111_05366_gb300 as goat  # noqa: E402
+
+
+def rel_fro(x, ref):
+    return float(np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def random_ds(n, seed, k=6):
+    rng = np.random.default_rng(seed)
+    P = np.zeros((n, n))
+    w = rng.random(k) + 0.1
+    w /= w.sum()
+    for t in range(k):
+        P[np.arange(n), rng.permutation(n)] += w[t]
+    return P
+
+
+def cuda(x, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+# ------------------------------------------------------------------ K1 GEMM
+
+@pytest.mark.parametrize("M,N,K,period", [(128, 256, 64, 64), (300, 520, 192, 192), (257, 255, 128, 64),
+                                          (1000, 700, 1024, 512)])
+def test_gemm_xyT_matches_exact_product(M, N, K, period):
+    rng = np.random.default_rng(M + N + K)
+    X = torch.from_numpy(rng.standard_normal((M, period)).astype(np.float32)).to(torch.bfloat16).cuda()
+    Y = torch.from_numpy(rng.standard_normal((N, K)).astype(np.float32)).to(torch.bfloat16).cuda()
+    out = goat.goat_gemm_bf16_xyT(X, Y, k_total=K, kx_period=period, scale=-2.0)
+    Xd = X.float().cpu().double().numpy()
+    Yd = Y.float().cpu().double().numpy()
+    Xk = np.concatenate([Xd] * (K // period), axis=1)   # X read at k mod period
+    ref = -2.0 * Xk @ Yd.T
+    assert rel_fro(out.cpu().double().numpy(), ref) < 1e-6
+
+
+# ------------------------------------------------------------------ gradient
+
+@pytest.mark.parametrize("n", [100, 300, 700])
+def test_gradient_fp32_form(n):
+    gp = synthetic.rho_er_pair(n, 0.1, 0.8, seed=n)
+    P = random_ds(n, 1).astype(np.float32)
+    G = goat.goat_gradient(cuda(gp.A), cuda(gp.B), cuda(P), precision=goat.GOAT_PREC_FP32)
+    ref = -oracle.gradient(gp.A, gp.B, P.astype(np.float64))
+    assert rel_fro(G.cpu().double().numpy(), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("n", [100, 300, 700])
+def test_gradient_bf16_form(n):
+    gp = synthetic.rho_er_pair(n, 0.1, 0.8, seed=n)
+    P = random_ds(n, 2).astype(np.float32)
+    G = goat.goat_gradient(cuda(gp.A), cuda(gp.B), cuda(P), precision=goat.GOAT_PREC_BF16)
+    ref = -oracle.gradient(gp.A, gp.B, P.astype(np.float64))
+    err = rel_fro(G.cpu().double().numpy(), ref)
+    assert err <= 2e-2
+    assert err <= 5e-3  # BF16 rounding of P and of Q B: ~1e-3 expected
+
+
+def test_gradient_at_permutation_is_exact_integer():
+    # at a permutation every product is an integer sum of 0/1 terms: exact in both forms
+    n = 333
+    gp = synthetic.rho_er_pair(n, 0.05, 0.9, seed=3)
+    P = np.zeros((n, n), np.float32)
+    P[np.arange(n), np.random.default_rng(0).permutation(n)] = 1
+    ref = -oracle.gradient(gp.A, gp.B, P.astype(np.float64))
+    for prec in (goat.GOAT_PREC_BF16, goat.GOAT_PREC_FP32):
+        G = goat.goat_gradient(cuda(gp.A), cuda(gp.B), cuda(P), precision=prec)
+        np.testing.assert_array_equal(G.cpu().double().numpy(), ref)
+
+
+def test_gradient_weighted_fp32_inputs():
+    n = 200
+    gp = synthetic.rho_er_pair(n, 0.1, 0.8, seed=5)
+    A = gp.A.astype(np.float32) * 3.0
+    B = gp.B.astype(np.float32) * 0.5
+    P = random_ds(n, 3).astype(np.float32)
+    G = goat.goat_gradient(cuda(A), cuda(B), cuda(P), precision=goat.GOAT_PREC_FP32)
+    ref = -oracle.gradient(A.astype(np.float64), B.astype(np.float64), P.astype(np.float64))
+    assert rel_fro(G.cpu().double().numpy(), ref) <= 1e-5
+
+
+# ------------------------------------------------------------------ Sinkhorn
+
+def _cost(n, seed):
+    gp = synthetic.rho_er_pair(n, 0.1, 0.8, seed=seed)
+    P = random_ds(n, seed)
+    return (-oracle.gradient(gp.A, gp.B, P)).astype(np.float32)
+
+
+@pytest.mark.parametrize("n,iters", [(100, 5), (300, 20), (517, 50)])
+def test_sinkhorn_fixed_iterations_match_oracle(n, iters):
+    G = _cost(n, n)
+    eps = 0.03 * float(np.abs(G).max())
+    rng = np.random.default_rng(n)
+    g0 = (rng.standard_normal(n) * eps).astype(np.float32)
+    f, g, Q, it, resid = goat.goat_sinkhorn(cuda(G), eps, 0.0, iters, g_init=cuda(g0), want_Q=True)
+    Qo, fo, go, ito, ro = oracle.lot_log(G.astype(np.float64), eps, 0.0, iters, g_init=g0.astype(np.float64))
+    assert it == ito == iters
+    np.testing.assert_allclose(f.cpu().double().numpy(), fo, atol=2e-3 * eps, rtol=0)
+    np.testing.assert_allclose(g.cpu().double().numpy(), go, atol=2e-3 * eps, rtol=0)
+    np.testing.assert_allclose(Q.cpu().double().numpy(), Qo, rtol=1e-3, atol=1e-6)
+    assert resid == pytest.approx(ro, rel=1e-2, abs=1e-5)
+
+
+@pytest.mark.parametrize("n", [64, 300])
+def test_sinkhorn_converges_to_tolerance(n):
+    G = _cost(n, 7)
+    eps = 0.03 * float(np.abs(G).max())
+    f, g, Q, it, resid = goat.goat_sinkhorn(cuda(G), eps, 1e-5, 5000, want_Q=True)
+    assert resid < 1e-5 and it < 5000
+    Qh = Q.cpu().double().numpy()
+    assert np.abs(Qh.sum(0) - 1).max() < 1e-4
+    assert np.abs(Qh.sum(1) - 1).max() < 1e-4
+    # same fixed point as the oracle (Sinkhorn's limit is unique)
+    Qo, *_ = oracle.lot(G.astype(np.float64), eps, 1e-10, 100000)
+    np.testing.assert_allclose(Qh, Qo, atol=5e-4)
+
+
+def test_sinkhorn_separable_cost_gives_barycenter():
+    n = 130
+    rng = np.random.default_rng(1)
+    G = (rng.random(n)[:, None] * 3 + rng.random(n)[None, :] * 5).astype(np.float32)
+    f, g, Q, it, resid = goat.goat_sinkhorn(cuda(G), 0.7, 1e-6, 100, want_Q=True)
+    np.testing.assert_allclose(Q.cpu().numpy(), np.full((n, n), 1.0 / n), atol=1e-6)
+
+
+def test_sinkhorn_rejects_non_finite_cost():
+    n = 64
+    G = _cost(n, 2)
+    G[3, 5] = np.nan
+    with pytest.raises(goat.GoatError) as e:
+        goat.goat_sinkhorn(cuda(G), 1.0, 1e-3, 50)
+    assert e.value.status == goat.GOAT_ERR_NAN
+
+
+# ------------------------------------------------------------------ line search and update
+
+@pytest.mark.parametrize("n", [60, 257])
+def test_line_search_matches_oracle(n):
+    gp = synthetic.rho_er_pair(n, 0.15, 0.8, seed=n)
+    A, B = gp.A.astype(np.float64), gp.B.astype(np.float64)
+    for seed in range(3):
+        P = random_ds(n, seed).astype(np.float32).astype(np.float64)
+        Q = random_ds(n, seed + 10).astype(np.float32).astype(np.float64)
+        G = -oracle.gradient(A, B, P)
+        GQ = -oracle.gradient(A, B, Q)
+        alpha, a, b = goat.goat_line_search(cuda(G.astype(np.float32)), cuda(GQ.astype(np.float32)),
+                                            cuda(P.astype(np.float32)), cuda(Q.astype(np.float32)))
+        alpha_p, a_o, b_p = oracle.step_size(A, B, P, Q)
+        # oracle: f(alpha P + (1-alpha) Q) = f(Q) + b_p alpha + a alpha^2 (alpha weights P);
+        # here  : f(P + t (Q - P)) = f(P) + b t + a t^2 (t weights Q): same a, b = -(b_p + 2a)
+        assert a == pytest.approx(a_o, rel=1e-4, abs=1e-6)
+        assert b == pytest.approx(-(b_p + 2 * a_o), rel=1e-4, abs=1e-6)
+        assert alpha == pytest.approx(1.0 - alpha_p, abs=1e-4)
+
+
+def test_fw_update_definition():
+    n = 203
+    rng = np.random.default_rng(0)
+    P, Q = rng.random((n, n)).astype(np.float32), rng.random((n, n)).astype(np.float32)
+    G, GQ = -rng.random((n, n)).astype(np.float32), -rng.random((n, n)).astype(np.float32)
+    Pt, Gt = cuda(P), cuda(G)
+    goat.goat_fw_update(Pt, Gt, cuda(Q), cuda(GQ), 0.375)
+    # paper's update with its alpha = 1 - 0.375 weighting P
+    np.testing.assert_allclose(Pt.cpu().numpy(), 0.625 * P + 0.375 * Q, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(Gt.cpu().numpy(), 0.625 * G + 0.375 * GQ, rtol=1e-6, atol=1e-7)
+
+
+# ------------------------------------------------------------------ projection (LAP)
+
+def test_project_paper_example(golden):
+    g = golden("paper_4x4_tie.txt")
+    M = np.array(g["matrix"], np.float32)
+    perm, cost, gap = goat.goat_project(cuda(M), maximize=False)
+    assert cost == g["value"][0]
+    assert tuple(perm.cpu().numpy()) in {tuple(int(x) for x in g["P1"]), tuple(int(x) for x in g["P2"])}
+    perm, cost, gap = goat.goat_project(cuda(M), maximize=True)
+    assert cost == oracle.lap(M.astype(np.float64), maximize=True)[1] == 183
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 64, 250, 513])
+def test_project_integer_matrices_bitwise(n):
+    rng = np.random.default_rng(n)
+    for mx in (True, False):
+        M = rng.integers(0, 20, size=(n, n)).astype(np.float32)  # many ties
+        perm, cost, gap = goat.goat_project(cuda(M), maximize=mx)
+        p = perm.cpu().numpy()
+        assert sorted(p) == list(range(n))
+        _, cost_o = oracle.lap(M.astype(np.float64), maximize=mx)
+        assert cost == cost_o
+        assert oracle.assignment_cost_f32(M, p) == cost
+
+
+@pytest.mark.parametrize("n", [100, 300, 1000])
+def test_project_real_matrices(n):
+    for seed, kind in enumerate(["uniform", "fig1", "relaxed"]):
+        rng = np.random.default_rng(seed + n)
+        if kind == "uniform":
+            M = rng.random((n, n)).astype(np.float32)
+        elif kind == "fig1":
+            M = synthetic.uniform_costs(n, 100, 150, seed, np.float32)
+        else:
+            M = random_ds(n, seed).astype(np.float32) + 1e-3 * rng.random((n, n)).astype(np.float32)
+        for mx in (True, False):
+            perm, cost, gap = goat.goat_project(cuda(M), maximize=mx)
+            p = perm.cpu().numpy()
+            assert sorted(p) == list(range(n))
+            _, cost_o = oracle.lap(M, maximize=mx)
+            tol = n * 2.0 ** -52 * float(np.abs(M).max()) * 4
+            assert abs(cost - cost_o) <= tol, (kind, mx, cost, cost_o)
+
+
+# ------------------------------------------------------------------ objective
+
+def test_objective_exact():
+    n = 500
+    gp = synthetic.rho_er_pair(n, 0.05, 0.8, seed=1)
+    perm = np.random.default_rng(2).permutation(n).astype(np.int32)
+    for p in (perm, gp.truth):
+        obj, dis = goat.goat_objective(cuda(gp.A), cuda(gp.B), cuda(p))
+        ref = oracle.objective_perm_u8(gp.A, gp.B, p)
+        assert obj == ref
+        assert dis == int(gp.A.sum()) + int(gp.B.sum()) - 2 * ref
+
+
+# ------------------------------------------------------------------ whole solve
+
+def test_match_rejects_asymmetric_input():
+    n = 50
+    gp = synthetic.rho_er_pair(n, 0.2, 0.9, seed=0)
+    A = gp.A.copy()
+    A[0, 1], A[1, 0] = 1, 0
+    with pytest.raises(goat.GoatError) as e:
+        goat.goat_match(cuda(A), cuda(gp.B))
+    assert e.value.status == goat.GOAT_ERR_INVALID_ARG
+
+
+def test_match_isomorphic_recovery():
+    for seed in range(3):
+        gp = synthetic.rho_er_pair(150, 0.1, 1.0, seed=seed)
+        perm, obj, st = goat.goat_match(cuda(gp.A), cuda(gp.B), max_iter=30, tol=1e-3)
+        assert (perm == gp.truth).all()
+        assert obj == gp.A.sum()
+
+
+@pytest.mark.parametrize("precision,warm", [(1, 0), (0, 1)])
+def test_match_accuracy_within_one_point_of_oracle(precision, warm):
+    # 20 seeds of the n = 100, p = 0.1, rho = 0.9 workload: mean matching accuracy
+    # and disagreements within 1 percentage point of the FP64 oracle's
+    acc, acc_o, dis, dis_o = [], [], [], []
+    prm = goat.default_params(precision=precision, sk_warm_start=warm, sk_tol=1e-3, sk_max_iter=500)
+    for seed in range(20):
+        gp = synthetic.rho_er_pair(100, 0.1, 0.9, seed=seed)
+        perm, obj, st = goat.goat_match(cuda(gp.A), cuda(gp.B), eps_rel=0.03, max_iter=30, tol=1e-3, params=prm)
+        ref = oracle.goat(gp.A, gp.B, eps_rel=0.03, max_iter=30, tol=1e-3, sk_tol=1e-3, sk_max_iter=500)
+        acc.append((perm == gp.truth).mean())
+        acc_o.append((ref["perm"] == gp.truth).mean())
+        edges = gp.A.sum() + gp.B.sum()
+        dis.append((edges - 2 * obj) / edges)
+        dis_o.append((edges - 2 * ref["objective"]) / edges)
+        assert obj == oracle.objective_perm(gp.A, gp.B, perm)
+    assert abs(np.mean(acc) - np.mean(acc_o)) <= 0.01
+    assert abs(np.mean(dis) - np.mean(dis_o)) <= 0.01
+
+
+def test_match_host_equals_device_call():
+    gp = synthetic.rho_er_pair(120, 0.1, 0.85, seed=4)
+    p1, o1, s1 = goat.goat_match(cuda(gp.A), cuda(gp.B), max_iter=10)
+    p2, o2, s2 = goat.goat_match_host(gp.A, gp.B, max_iter=10)
+    assert (p1 == p2).all() and o1 == o2 and s1["fw_iters"] == s2["fw_iters"]
+
+
+def test_match_project_on_gradient_and_init():
+    gp = synthetic.rho_er_pair(90, 0.15, 1.0, seed=6)
+    prm = goat.default_params(project_on_grad=1)
+    perm, obj, st = goat.goat_match(cuda(gp.A), cuda(gp.B), params=prm)
+    assert (perm == gp.truth).all()
+    init = np.full((90, 90), 1 / 90, np.float32) * 0.5 + random_ds(90, 1).astype(np.float32) * 0.5
+    perm, obj, st = goat.goat_match(cuda(gp.A), cuda(gp.B), init=cuda(init))
+    assert obj == oracle.objective_perm(gp.A, gp.B, perm)
