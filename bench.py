@@ -1,0 +1,460 @@
+#!/usr/bin/env python
+"""GOAT Frank-Wolfe throughput on GB300.
+
+Workload: one rho-correlated 3-block SBM pair (blocks 40/35/25 %, p_in = 0.02,
+p_out = 0.004, rho = 0.7, B vertex-permuted by a seeded sigma), n = 32768,
+barycenter init, up to 30 Frank-Wolfe iterations, final GPU linear assignment.
+A "step" is one whole solve (goat_match: gradient products, Sinkhorn, line
+search, update for every FW iteration, then the projection and the exact
+objective).  The metric is FW iterations per second of the chosen form
+(BF16 tensor-core products, FP32 log-domain Sinkhorn warm-started from the
+previous step's duals), reported next to the plain FP32-accurate GPU form
+(two-term BF16 split products, cold-started Sinkhorn) at the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own pair (seed + rank): replicas, weak scaling.
+The reference arm (--impl reference) times the FP64 CPU oracle on a bounded
+row sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GOAT FW iters/s at n=32768, chosen vs plain FP32 on GB300 at equal match accuracy"
+UNIT = "FW iters/s"
+T0 = time.time()
+
+
+def log(msg: str):
+    print(f"[bench {time.time() - T0:7.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--max-iter", type=int, default=30)
+    ap.add_argument("--fw-tol", type=float, default=1e-4)
+    ap.add_argument("--sk-tol", type=float, default=1e-3)
+    ap.add_argument("--sk-max-iter", type=int, default=500)
+    ap.add_argument("--seed", type=int, default=3000)
+    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-rows", type=int, default=4)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-case", choices=["gemm", "sinkhorn", "lap"], default=None,
+                    help="run only one step kind a few times on the workload (the small cases profiled with ncu)")
+    ap.add_argument("--repeat", type=int, default=3)
+    return ap.parse_args()
+
+
+def workload_config(args):
+    return {"workload": f"rho-SBM pair, 3 blocks (40/35/25%), n={args.n}, p_in=0.02, p_out=0.004, rho=0.7, "
+                        f"B vertex-permuted; barycenter init; <= {args.max_iter} FW iters; GPU LAP projection",
+            "n": args.n, "max_fw_iters": args.max_iter, "fw_tol": args.fw_tol, "eps_rel": 0.03,
+            "sinkhorn_tol": args.sk_tol, "sinkhorn_max_iter": args.sk_max_iter, "seed": args.seed,
+            "l2": "inputs larger than L2 (FP32 G and P are 4.3 GB each at n=32768)"}
+
+
+# ------------------------------------------------------------------ clocks
+
+QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    """Samples nvidia-smi every 200 ms while the timed region runs."""
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = f"/tmp/goat_clocks_{os.getpid()}.csv"
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [x for x in sm if x > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ peaks / profiles
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": d.get("hbm_gbs"), "bf16_tflops": d.get("bf16_tflops"),
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained"), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def gemm_traffic_per_launch(n: int):
+    """DRAM bytes per GEMM launch from the committed ncu summary, scaled to n, or None.
+
+    The summary records the kernel source hash it was taken with; a changed
+    kernel invalidates it."""
+    path = os.path.join(ROOT, "profiles", "k_gemm_xyT_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    src = open(os.path.join(ROOT, "paper_2111_05366_gb300", "csrc", "goat_gemm.cu"), "rb").read()
+    if kv.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    try:
+        bytes_ = float(kv["dram_bytes_per_launch"])
+        n_cap = float(kv["n"])
+    except (KeyError, ValueError):
+        return None
+    # the products are n x n x n: operand re-reads grow like n^3 / tile, outputs like n^2
+    return bytes_ * (n / n_cap) ** 3 if n != n_cap else bytes_
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+
+def cpu_oracle_sample(gp, rows: int, sk_iters_per_fw: float):
+    """Times the FP64 oracle on a row sample of one FW iteration of the workload.
+
+    Work timed: `rows` rows of grad f(J) (oracle.gradient_rows, naive loops), and
+    the Sinkhorn row scaling of those rows.  Scaled to one FW iteration as
+    T = (n / rows) * (2 * T_grad + 2 * k_sk * T_rowlse): the step size of the oracle
+    forms the same naive products as the gradient (counted as a second gradient),
+    and a Sinkhorn iteration is a row pass plus a column pass of equal work."""
+    import oracle
+    n = gp.n
+    rng = np.random.default_rng(0)
+    sel = np.sort(rng.choice(n, size=rows, replace=False)).astype(np.int32)
+    P = np.full((n, n), 1.0 / n, dtype=np.float32)
+    t0 = time.perf_counter()
+    grad = oracle.gradient_rows(gp.A, gp.B, P, sel)
+    t_grad = time.perf_counter() - t0
+    del P
+    G_rows = (-grad).astype(np.float32)
+    eps = 0.03 * float(np.abs(G_rows).max())
+    g = np.zeros(n, dtype=np.float32)
+    t0 = time.perf_counter()
+    oracle.lot_rows(G_rows, g, eps)
+    t_lse = time.perf_counter() - t0
+    t_iter = (n / rows) * (2.0 * t_grad + 2.0 * sk_iters_per_fw * t_lse)
+    sample = (f"{rows} rows of grad f at the barycenter (naive FP64 loops) + their Sinkhorn row scaling, "
+              f"n={n}; one FW iteration = (n/rows) x (2 x gradient rows + 2 x {sk_iters_per_fw:.1f} x row-LSE); "
+              f"measured {t_grad + t_lse:.1f} s")
+    return {"value": 1.0 / t_iter, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+            "seconds_per_fw_iter": t_iter}
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2111_05366_gb300 import synthetic
+    gp = synthetic.large_sbm_pair(args.n, seed=args.seed)
+    vals = []
+    last = None
+    for step in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(gp, args.cpu_rows, 50.0)
+        if step >= args.warmup:
+            vals.append(r["value"])
+        last = r
+    v = float(np.mean(vals))
+    cb = dict(last)
+    cb["value"] = v
+    cb["sample"] = last["sample"] + "; Sinkhorn iterations per FW iteration assumed 50"
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args),
+            "impl": "reference", "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ single-kernel cases (for ncu)
+
+def run_kernel_case(args):
+    """Calls one step of the path `--repeat` times on the workload pair at size --n.
+
+    gemm:     goat_gradient at a doubly stochastic P (two tensor-core products per call)
+    sinkhorn: goat_sinkhorn on -grad f(J) for a fixed number of iterations (tol 0)
+    lap:      goat_project on the entropic direction Q at the barycenter (a diffuse,
+              degree-structured doubly stochastic matrix like the relaxed P of a hard pair)"""
+    import torch
+
+    import paper_2111_05366_gb300 as goat
+    from paper_2111_05366_gb300 import synthetic
+    torch.cuda.set_device(0)
+    goat.load()
+    n = args.n
+    gp = synthetic.large_sbm_pair(n, seed=args.seed)
+    A = torch.from_numpy(gp.A).cuda()
+    B = torch.from_numpy(gp.B).cuda()
+    P = torch.full((n, n), 1.0 / n, dtype=torch.float32, device="cuda")
+    P[torch.arange(n, device="cuda"), torch.randperm(n, device="cuda")] += 1.0
+    P /= 2.0
+    out = {"case": args.kernel_case, "n": n}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.kernel_case == "gemm":
+        G = goat.goat_gradient(A, B, P)
+        e0.record()
+        for _ in range(args.repeat):
+            goat.goat_gradient(A, B, P, out=G)
+        e1.record()
+    elif args.kernel_case == "sinkhorn":
+        G = goat.goat_gradient(A, B, P)
+        eps = 0.03 * float(G.abs().max())
+        e0.record()
+        for _ in range(args.repeat):
+            goat.goat_sinkhorn(G, eps, 0.0, 10)
+        e1.record()
+    else:
+        J = torch.full((n, n), 1.0 / n, dtype=torch.float32, device="cuda")
+        G = goat.goat_gradient(A, B, J)
+        del J
+        eps = 0.03 * float(G.abs().max())
+        _, _, Q, _, _ = goat.goat_sinkhorn(G, eps, args.sk_tol, args.sk_max_iter, want_Q=True)
+        del G
+        e0.record()
+        for _ in range(args.repeat):
+            _, cost, gap = goat.goat_project(Q, allow_uncertified=True)
+        e1.record()
+        out["cost"], out["gap"] = cost, gap
+    torch.cuda.synchronize()
+    out["ms_per_call"] = e0.elapsed_time(e1) / args.repeat
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.kernel_case:
+        return run_kernel_case(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2111_05366_gb300 as goat
+    from paper_2111_05366_gb300 import synthetic
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    goat.load()
+    n = args.n
+    log(f"generating the n={n} pair")
+    gp = synthetic.large_sbm_pair(n, seed=args.seed + rank)
+    log(f"pair ready: {int(gp.A.sum())} + {int(gp.B.sum())} nonzeros")
+    A = torch.from_numpy(gp.A).cuda()
+    B = torch.from_numpy(gp.B).cuda()
+    ws = torch.empty(goat.workspace_bytes(n, goat.GOAT_DTYPE_U8, goat.GOAT_PREC_FP32), dtype=torch.uint8,
+                     device="cuda")
+    chosen = goat.default_params(precision=goat.GOAT_PREC_BF16, sk_warm_start=1, sk_tol=args.sk_tol,
+                                 sk_max_iter=args.sk_max_iter, profile=1)
+    plain = goat.default_params(precision=goat.GOAT_PREC_FP32, sk_warm_start=0, sk_tol=args.sk_tol,
+                                sk_max_iter=args.sk_max_iter, profile=1)
+
+    def solve(params):
+        return goat.goat_match(A, B, eps_rel=0.03, max_iter=args.max_iter, tol=args.fw_tol, params=params,
+                               workspace=ws)
+
+    def timed(params, warmup, steps, sampler=None):
+        for _ in range(warmup):
+            _, _, stw = solve(params)
+            log(f"warmup solve: {stw['fw_iters']} FW iters, {stw['ms_total']:.0f} ms "
+                f"(fw {stw['ms_fw']:.0f}, project {stw['ms_project']:.0f}, lap rounds {stw['lap_rounds']})")
+        barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        outs = [solve(params) for _ in range(steps)]
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        ms = e0.elapsed_time(e1)
+        return ms, outs, clocks
+
+    sampler = ClockSampler(local)
+    ms, outs, clocks = timed(chosen, args.warmup, args.steps, sampler)
+    log(f"chosen form timed: {ms:.0f} ms for {args.steps} solves")
+    fw_iters = sum(o[2]["fw_iters"] for o in outs)
+    ms_max = max_over_ranks(ms)
+    iters_all = sum_over_ranks(float(fw_iters))
+    value = iters_all / (ms_max / 1000.0)
+    st = outs[-1][2]
+    acc = float((outs[-1][0] == gp.truth).mean())
+
+    # per-phase breakdown and the roofline of the dominant kernel (the tensor-core products)
+    ms_gemm = sum(o[2]["ms_gemm"] for o in outs)
+    n_gemm = sum(o[2]["gemm_launches"] for o in outs)
+    ms_sk = sum(o[2]["ms_sinkhorn"] for o in outs)
+    ms_step = sum(o[2]["ms_step"] for o in outs)
+    ms_proj = sum(o[2]["ms_project"] for o in outs)
+    sk_total = sum(o[2]["sk_iters_total"] for o in outs)
+    launches = sum(o[2]["launches"] for o in outs)
+    peaks = measured_peaks()
+    flop_per_launch = 2.0 * n ** 3
+    achieved = flop_per_launch / (ms_gemm / max(n_gemm, 1) / 1000.0) / 1e12
+    peak = peaks["bf16_tflops_sustained"]
+    traffic = gemm_traffic_per_launch(n)
+    roofline = {"bound": "tensor", "kernel": "k_gemm_xyT (BF16 kind::f16, one n x n x n product per launch)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": f"{peaks['source']} bf16_tflops_sustained",
+                "algorithmic_flop_per_launch": flop_per_launch}
+
+    breakdown = {"ms_per_fw_iter": ms / max(fw_iters, 1), "gemm_ms_per_launch": ms_gemm / max(n_gemm, 1),
+                 "gemm_share": ms_gemm / ms, "sinkhorn_share": ms_sk / ms, "step_share": ms_step / ms,
+                 "projection_share": ms_proj / ms, "sinkhorn_iters_per_fw_iter": sk_total / max(fw_iters, 1),
+                 "fw_iters_per_solve": fw_iters / args.steps, "accuracy": acc,
+                 "objective": st["objective"], "disagreements": st["disagreements"], "lap_gap": st["lap_gap"],
+                 "lap_rounds": st["lap_rounds"]}
+    if sk_total:
+        # one Sinkhorn iteration reads G twice (row pass + column pass): 8 n^2 bytes
+        breakdown["sinkhorn_gbs_two_pass"] = 8.0 * n * n / (ms_sk / sk_total / 1000.0) / 1e9
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+              "config": workload_config(args), "clocks": clocks, "gpu_launches": int(sum_over_ranks(launches)),
+              "roofline": roofline, "breakdown": breakdown}
+
+    # plain FP32-accurate GPU form on the same pair
+    if not args.no_plain:
+        ms_p, outs_p, _ = timed(plain, 1, args.plain_steps)
+        log(f"plain form timed: {ms_p:.0f} ms")
+        it_p = sum(o[2]["fw_iters"] for o in outs_p)
+        v_p = sum_over_ranks(float(it_p)) / (max_over_ranks(ms_p) / 1000.0)
+        result["plain_fp32"] = {"value": v_p, "unit": UNIT, "accuracy": float((outs_p[-1][0] == gp.truth).mean()),
+                                "fw_iters_per_solve": it_p / args.plain_steps,
+                                "sinkhorn_iters_per_fw_iter": sum(o[2]["sk_iters_total"] for o in outs_p) / max(it_p, 1),
+                                "gemm_ms_per_launch": sum(o[2]["ms_gemm"] for o in outs_p) /
+                                max(sum(o[2]["gemm_launches"] for o in outs_p), 1)}
+        result["chosen_over_plain"] = value / v_p
+
+    # end to end through the host-buffer entry point: pinned host A, B in, permutation out
+    if not args.no_e2e:
+        Ah = torch.from_numpy(gp.A).pin_memory().numpy()
+        Bh = torch.from_numpy(gp.B).pin_memory().numpy()
+        ws_h = torch.empty(goat.workspace_bytes(n, goat.GOAT_DTYPE_U8, goat.GOAT_PREC_BF16, host=True),
+                           dtype=torch.uint8, device="cuda")
+        del ws
+        torch.cuda.empty_cache()
+        goat.goat_match_host(Ah, Bh, eps_rel=0.03, max_iter=args.max_iter, tol=args.fw_tol, params=chosen,
+                             workspace=ws_h)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        it_e = 0
+        for _ in range(args.e2e_steps):
+            perm_h, obj_h, st_h = goat.goat_match_host(Ah, Bh, eps_rel=0.03, max_iter=args.max_iter,
+                                                       tol=args.fw_tol, params=chosen, workspace=ws_h)
+            it_e += st_h["fw_iters"]
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ms_e = max_over_ranks(e0.elapsed_time(e1))
+        result["e2e"] = {"value": sum_over_ranks(float(it_e)) / (ms_e / 1000.0), "unit": UNIT,
+                         "h2d_bytes_per_step": int(2 * n * n), "d2h_bytes_per_step": int(4 * n),
+                         "api": "goat_match_host (pinned host A, B; permutation read back)"}
+
+    if not args.no_e2e:
+        log("e2e done")
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        log("timing the CPU oracle sample")
+        result["cpu_baseline"] = cpu_oracle_sample(gp, args.cpu_rows, breakdown["sinkhorn_iters_per_fw_iter"])
+        result["cpu_baseline"]["cores"] = 1
+
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -91,6 +91,7 @@ typedef struct goat_params {
     int sk_check_every;   /* Sinkhorn iterations between host convergence checks, default 8 */
     int project_on_grad;  /* 0: final LAP on P (default); 1: on grad f(P) (the paper's Alg. 3 line) */
     int lap_max_rounds;   /* cap on auction bidding rounds over all phases, default 1<<20 */
+    int profile;          /* 1: time the phases with CUDA events on `stream` (stats ms_*), default 0 */
 } goat_params;
 
 typedef struct goat_stats {
@@ -105,6 +106,12 @@ typedef struct goat_stats {
     double lap_gap;                    /* dual - primal of the final LAP (0: certified)     */
     int lap_rounds;                    /* auction rounds used                               */
     float ms_total, ms_fw, ms_project; /* device time of the whole call, FW loop, projection */
+    /* with params.profile = 1 (else 0): device time per phase, summed over the FW loop */
+    float ms_gemm;                     /* the tensor-core products (gemm_launches launches)  */
+    int gemm_launches;
+    float ms_sinkhorn;                 /* Sinkhorn solves, host polls included              */
+    float ms_step;                     /* Q materialisation, line search and update          */
+    long long launches;                /* kernels launched by the call                       */
 } goat_stats;
 
 /* Fills *p with the defaults listed above. */
@@ -116,6 +123,10 @@ GOAT_API const char *goat_strerror(int status);
 /* Bytes of scratch the calls below need for size n (the maximum over calls).
  * Returns 0 for n < 1. */
 GOAT_API size_t goat_workspace_bytes(int n, int dtype_AB, int precision);
+
+/* Bytes of scratch goat_match_host needs (goat_workspace_bytes plus the device
+ * copies of A, B and init).  Returns 0 for n < 1. */
+GOAT_API size_t goat_workspace_bytes_host(int n, int dtype_AB, int precision);
 
 /*
  * goat_match -- the whole GOAT solve (Alg. 3).
@@ -135,7 +146,8 @@ GOAT_API int goat_match(const void *A, const void *B, int n, int dtype_AB, const
                void *workspace, size_t workspace_bytes, goat_stream_t stream);
 
 /* goat_match with A, B, init in HOST memory (pageable or pinned); the copies to
- * the device are part of the call. */
+ * the device are part of the call.  Its workspace must hold
+ * goat_workspace_bytes_host(n, dtype_AB, precision) bytes (it stages the copies). */
 GOAT_API int goat_match_host(const void *A_host, const void *B_host, int n, int dtype_AB, const float *init_host,
                     float eps_rel, int max_iter, float tol, const goat_params *p, int32_t *perm_out,
                     double *objective_out, goat_stats *stats, void *workspace, size_t workspace_bytes,

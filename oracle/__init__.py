@@ -66,9 +66,8 @@ def _load():
                                           _dp, _dp, _dp, _dp, _dp]),
             "oracle_lot_log": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_int, _dp, _dp, _dp, _dp]),
-            "oracle_lot_rows_f32": (None, [_fp, ctypes.c_int, _fp, ctypes.c_double, _ip, ctypes.c_int, _dp]),
-            "oracle_lot_colsums_f32": (None, [_fp, ctypes.c_int, _fp, _fp, ctypes.c_double, _ip,
-                                              ctypes.c_int, _dp]),
+            "oracle_lot_rows_f32": (None, [_fp, ctypes.c_int, ctypes.c_int, _fp, ctypes.c_double, _dp]),
+            "oracle_lot_colsums_f32": (None, [_fp, ctypes.c_int, ctypes.c_int, _fp, _fp, ctypes.c_double, _dp]),
             "oracle_step_size": (ctypes.c_double, [_dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
             "oracle_lap_min": (ctypes.c_double, [_dp, ctypes.c_int, _ip, _dp, _dp]),
             "oracle_lap": (ctypes.c_double, [_dp, ctypes.c_int, ctypes.c_int, _ip]),
@@ -210,22 +209,22 @@ def lot_log(M, eps: float, tol: float, max_iter: int, g_init=None):
     return Q, f, g, it, r.value
 
 
-def lot_rows(M, g, eps: float, rows) -> np.ndarray:
-    """Row scaling f_i = -eps LSE_j((g_j - M_ij)/eps) on selected rows (FP64)."""
-    M, g, rows = _f(M), _f(g), _i(rows)
-    n = M.shape[0]
-    out = np.empty(len(rows))
-    _load().oracle_lot_rows_f32(_ptr(M, _fp), n, _ptr(g, _fp), eps, _ptr(rows, _ip), len(rows), _ptr(out, _dp))
+def lot_rows(M_rows, g, eps: float) -> np.ndarray:
+    """Row scaling f_r = -eps LSE_j((g_j - M_rj)/eps) on a block of rows (nrows x n), FP64."""
+    M_rows, g = _f(M_rows), _f(g)
+    nrows, n = M_rows.shape
+    out = np.empty(nrows)
+    _load().oracle_lot_rows_f32(_ptr(M_rows, _fp), nrows, n, _ptr(g, _fp), eps, _ptr(out, _dp))
     return out
 
 
-def lot_colsums(M, f, g, eps: float, cols) -> np.ndarray:
-    """Column sums sum_i exp((f_i + g_j - M_ij)/eps) on selected columns (FP64)."""
-    M, f, g, cols = _f(M), _f(f), _f(g), _i(cols)
-    n = M.shape[0]
-    out = np.empty(len(cols))
-    _load().oracle_lot_colsums_f32(_ptr(M, _fp), n, _ptr(f, _fp), _ptr(g, _fp), eps, _ptr(cols, _ip),
-                                   len(cols), _ptr(out, _dp))
+def lot_colsums(M_cols, f, g_cols, eps: float) -> np.ndarray:
+    """Column sums sum_i exp((f_i + g_c - M_ic)/eps) on a block of columns (n x ncols), FP64."""
+    M_cols, f, g_cols = _f(M_cols), _f(f), _f(g_cols)
+    n, ncols = M_cols.shape
+    out = np.empty(ncols)
+    _load().oracle_lot_colsums_f32(_ptr(M_cols, _fp), n, ncols, _ptr(f, _fp), _ptr(g_cols, _fp), eps,
+                                   _ptr(out, _dp))
     return out
 
 

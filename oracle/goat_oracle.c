@@ -322,13 +322,12 @@ int oracle_lot_log(const double *M, int n, double eps, double tol, int max_iter,
     return it;
 }
 
-/* Row scaling of the log-domain iteration on selected rows of a large
- * single-precision cost:  f_i = -eps LSE_j((g_j - M_ij)/eps). */
-void oracle_lot_rows_f32(const float *M, int n, const float *g, double eps, const int *rows, int nrows, double *f_out)
+/* Row scaling of the log-domain iteration on a block of rows of a large
+ * single-precision cost (Mrows is nrows x n):  f_r = -eps LSE_j((g_j - M_rj)/eps). */
+void oracle_lot_rows_f32(const float *Mrows, int nrows, int n, const float *g, double eps, double *f_out)
 {
     for (int r = 0; r < nrows; ++r) {
-        int i = rows[r];
-        const float *mi = M + IDX(i, 0, n);
+        const float *mi = Mrows + IDX(r, 0, n);
         double m = -INFINITY;
         for (int j = 0; j < n; ++j) { double x = ((double)g[j] - (double)mi[j]) / eps; if (x > m) m = x; }
         double s = 0.0;
@@ -337,15 +336,15 @@ void oracle_lot_rows_f32(const float *M, int n, const float *g, double eps, cons
     }
 }
 
-/* Column sums S_j = sum_i exp((f_i + g_j - M_ij)/eps) on selected columns. */
-void oracle_lot_colsums_f32(const float *M, int n, const float *f, const float *g, double eps,
-                            const int *cols, int ncols, double *S_out)
+/* Column sums S_c = sum_i exp((f_i + g_c - M_ic)/eps) on a block of columns
+ * (Mcols is n x ncols, row-major: Mcols[i][c] = M[i][column c]). */
+void oracle_lot_colsums_f32(const float *Mcols, int n, int ncols, const float *f, const float *gcols, double eps,
+                            double *S_out)
 {
     for (int c = 0; c < ncols; ++c) {
-        int j = cols[c];
         double s = 0.0;
         for (int i = 0; i < n; ++i)
-            s += exp(((double)f[i] + (double)g[j] - (double)M[IDX(i, j, n)]) / eps);
+            s += exp(((double)f[i] + (double)gcols[c] - (double)Mcols[IDX(i, c, ncols)]) / eps);
         S_out[c] = s;
     }
 }

@@ -34,7 +34,8 @@ GOAT_PREC_BF16 = 0
 GOAT_PREC_FP32 = 1
 GOAT_TRACE_MAX = 256
 
-EXPORTED = ["goat_default_params", "goat_strerror", "goat_workspace_bytes", "goat_match", "goat_match_host",
+EXPORTED = ["goat_default_params", "goat_strerror", "goat_workspace_bytes", "goat_workspace_bytes_host",
+            "goat_match", "goat_match_host",
             "goat_gradient", "goat_sinkhorn", "goat_line_search", "goat_fw_update", "goat_project",
             "goat_objective", "goat_gemm_bf16_xyT"]
 
@@ -48,7 +49,7 @@ class GoatError(RuntimeError):
 class goat_params(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("sk_max_iter", ctypes.c_int), ("sk_tol", ctypes.c_float),
                 ("sk_warm_start", ctypes.c_int), ("sk_check_every", ctypes.c_int),
-                ("project_on_grad", ctypes.c_int), ("lap_max_rounds", ctypes.c_int)]
+                ("project_on_grad", ctypes.c_int), ("lap_max_rounds", ctypes.c_int), ("profile", ctypes.c_int)]
 
 
 class goat_stats(ctypes.Structure):
@@ -56,7 +57,9 @@ class goat_stats(ctypes.Structure):
                 ("sk_iters", ctypes.c_int * GOAT_TRACE_MAX), ("sk_resid", ctypes.c_float * GOAT_TRACE_MAX),
                 ("alpha", ctypes.c_double * GOAT_TRACE_MAX), ("objective", ctypes.c_double),
                 ("disagreements", ctypes.c_double), ("lap_gap", ctypes.c_double), ("lap_rounds", ctypes.c_int),
-                ("ms_total", ctypes.c_float), ("ms_fw", ctypes.c_float), ("ms_project", ctypes.c_float)]
+                ("ms_total", ctypes.c_float), ("ms_fw", ctypes.c_float), ("ms_project", ctypes.c_float),
+                ("ms_gemm", ctypes.c_float), ("gemm_launches", ctypes.c_int), ("ms_sinkhorn", ctypes.c_float),
+                ("ms_step", ctypes.c_float), ("launches", ctypes.c_longlong)]
 
 
 _lock = threading.Lock()
@@ -81,6 +84,7 @@ def load():
             "goat_default_params": (None, [ctypes.POINTER(goat_params)]),
             "goat_strerror": (ctypes.c_char_p, [_i]),
             "goat_workspace_bytes": (ctypes.c_size_t, [_i, _i, _i]),
+            "goat_workspace_bytes_host": (ctypes.c_size_t, [_i, _i, _i]),
             "goat_match": (_i, [_vp, _vp, _i, _i, _vp, _f, _i, _f, ctypes.POINTER(goat_params), _vp,
                                 ctypes.POINTER(_d), ctypes.POINTER(goat_stats), _vp, ctypes.c_size_t, _vp]),
             "goat_match_host": (_i, [_vp, _vp, _i, _i, _vp, _f, _i, _f, ctypes.POINTER(goat_params), _vp,
@@ -159,8 +163,11 @@ def default_params(**overrides) -> goat_params:
     return p
 
 
-def workspace_bytes(n: int, dtype_AB: int = GOAT_DTYPE_U8, precision: int = GOAT_PREC_BF16) -> int:
-    return int(load().goat_workspace_bytes(int(n), int(dtype_AB), int(precision)))
+def workspace_bytes(n: int, dtype_AB: int = GOAT_DTYPE_U8, precision: int = GOAT_PREC_BF16,
+                    host: bool = False) -> int:
+    """Scratch bytes goat_match (host=False) or goat_match_host (host=True) needs for size n."""
+    fn = load().goat_workspace_bytes_host if host else load().goat_workspace_bytes
+    return int(fn(int(n), int(dtype_AB), int(precision)))
 
 
 def _stats_dict(st: goat_stats) -> dict:
@@ -168,7 +175,9 @@ def _stats_dict(st: goat_stats) -> dict:
     return {"fw_iters": st.fw_iters, "converged": bool(st.converged), "sk_iters_total": st.sk_iters_total,
             "sk_iters": list(st.sk_iters[:k]), "sk_resid": list(st.sk_resid[:k]), "alpha": list(st.alpha[:k]),
             "objective": st.objective, "disagreements": st.disagreements, "lap_gap": st.lap_gap,
-            "lap_rounds": st.lap_rounds, "ms_total": st.ms_total, "ms_fw": st.ms_fw, "ms_project": st.ms_project}
+            "lap_rounds": st.lap_rounds, "ms_total": st.ms_total, "ms_fw": st.ms_fw, "ms_project": st.ms_project,
+            "ms_gemm": st.ms_gemm, "gemm_launches": st.gemm_launches, "ms_sinkhorn": st.ms_sinkhorn,
+            "ms_step": st.ms_step, "launches": st.launches}
 
 
 # ---------------------------------------------------------------- entry points

@@ -38,7 +38,7 @@ static Plan make_plan(int n, int dtype, int precision, int need) {
     w.ld = operand_ld(n);
     w.terms = precision == GOAT_PREC_FP32 ? 2 : 1;
     w.state = take(sizeof(DevState));
-    w.cost = take(8 * sizeof(double));  // [0,3) u64 sums, [3,6) f64 sums, [6] assignment cost
+    w.cost = take(16 * sizeof(double));  // [0,3) u64 sums, [3,6) f64 sums, [6] assignment cost, [7,10) LAP bound
     if (need & (NEED_GEMM | NEED_FW)) {
         w.A16 = take((size_t)n * w.ld * 2);
         w.B16 = take((size_t)n * w.ld * 2);
@@ -73,6 +73,10 @@ static Plan make_plan(int n, int dtype, int precision, int need) {
 }
 
 // ---------------------------------------------------------------- helpers
+
+static thread_local long long t_launches = 0;
+void note_launches(int k) { t_launches += k; }
+long long launches_so_far() { return t_launches; }
 
 static int device_ok() {
     static int status = 1;  // 1 = unknown
@@ -140,6 +144,7 @@ __global__ void k_state_init(DevState *st, float eps_rel, int maximize, float fw
 static int init_state(DevState *st, float eps_rel, int maximize, float fw_tol, cudaStream_t s) {
     if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return GOAT_ERR_CUDA;
     k_state_init<<<1, 1, 0, s>>>(st, eps_rel, maximize, fw_tol);
+    note_launches(1);
     return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
 }
 
@@ -156,7 +161,8 @@ static int cuda_status(cudaError_t e) {
 }
 
 // -grad f(X) = -2 A X B for symmetric A, B, with X already in the split-term buffer Xq.
-static int gradient_from_terms(const Plan &w, const Scratch &ws, int n, float *G_out, int *err, cudaStream_t s) {
+static int gradient_from_terms(const Plan &w, const Scratch &ws, int n, float *G_out, int *err, cudaStream_t s,
+                               cudaEvent_t between = nullptr) {
     GemmCall c1;
     std::memset(&c1, 0, sizeof(c1));
     c1.X = ws.at<__nv_bfloat16>(w.B16);
@@ -179,6 +185,7 @@ static int gradient_from_terms(const Plan &w, const Scratch &ws, int n, float *G
     c1.out_cols = w.ld;  // the padding columns receive zeros
     c1.err = err;
     GOAT_TRY(gemm_xyT(c1, s));
+    if (between) cudaEventRecord(between, s);
 
     GemmCall c2 = c1;
     c2.X = ws.at<__nv_bfloat16>(w.A16);
@@ -233,6 +240,7 @@ static int match_impl(const void *A, const void *B, int n, int dtype, const floa
     } evg{ev};
     cudaEventRecord(ev[0], s);
 
+    const long long launches0 = launches_so_far();
     GOAT_TRY(init_state(st, eps_rel, 1, tol, s));
     GOAT_TRY(prepare_operands(A, B, n, dtype, w, ws, st, degA, degB, pinned, s));
 
@@ -248,18 +256,50 @@ static int match_impl(const void *A, const void *B, int n, int dtype, const floa
     GOAT_TRY(cuda_status(cudaGetLastError()));
     cudaEventRecord(ev[1], s);
 
+    const bool prof = prm.profile != 0;
+    cudaEvent_t pe[6] = {};  // s0 | sinkhorn | s1 | write_q | g0 | gemm1 | g1 | gemm2 | g2 | step | u1
+    if (prof)
+        for (auto &e : pe) cudaEventCreate(&e);
+    struct ProfGuard {
+        cudaEvent_t *e;
+        bool on;
+        ~ProfGuard() {
+            if (on)
+                for (int k = 0; k < 6; ++k) cudaEventDestroy(e[k]);
+        }
+    } pg{pe, prof};
+    float ms_gemm = 0.f, ms_sk = 0.f, ms_step = 0.f;
+    int gemm_launches = 0;
+
     int it = 0, converged = 0;
     for (; it < max_iter; ++it) {
+        if (prof) cudaEventRecord(pe[0], s);
         sinkhorn_begin(st, -1.0f, prm.sk_tol, prm.sk_warm_start ? nullptr : g, n, s);
         GOAT_TRY(sinkhorn_solve(G, n, n, f, g, partial, st, prm.sk_max_iter, prm.sk_check_every, pinned, s));
+        if (prof) cudaEventRecord(pe[1], s);
         write_q(G, n, n, f, g, st, Xq, w.ld, w.terms, nullptr, 0, s);
-        GOAT_TRY(gradient_from_terms(w, ws, n, GQ, &st->error, s));
+        if (prof) cudaEventRecord(pe[2], s);
+        GOAT_TRY(gradient_from_terms(w, ws, n, GQ, &st->error, s, prof ? pe[3] : nullptr));
+        if (prof) cudaEventRecord(pe[4], s);
         line_search(G, GQ, P, Xq, w.ld, w.terms, nullptr, n, partial, st, s);
         fw_update(P, G, GQ, Xq, w.ld, w.terms, nullptr, n, st, 0.0f, &st->gmax_next, s);
         fw_roll(st, s);
+        if (prof) cudaEventRecord(pe[5], s);
         GOAT_TRY(cuda_status(cudaMemcpyAsync(pinned, &st->fw_done, sizeof(int), cudaMemcpyDeviceToHost, s)));
         GOAT_TRY(cuda_status(cudaMemcpyAsync(pinned + 1, &st->error, sizeof(int), cudaMemcpyDeviceToHost, s)));
         GOAT_TRY(cuda_status(cudaStreamSynchronize(s)));
+        if (prof) {
+            float a = 0.f, b = 0.f, c = 0.f, d = 0.f, e = 0.f;
+            cudaEventElapsedTime(&a, pe[0], pe[1]);
+            cudaEventElapsedTime(&b, pe[1], pe[2]);
+            cudaEventElapsedTime(&c, pe[2], pe[3]);
+            cudaEventElapsedTime(&d, pe[3], pe[4]);
+            cudaEventElapsedTime(&e, pe[4], pe[5]);
+            ms_sk += a;
+            ms_step += b + e;
+            ms_gemm += c + d;
+            gemm_launches += 2;
+        }
         if (pinned[1]) return pinned[1];
         if (pinned[0]) {
             converged = 1;
@@ -325,6 +365,11 @@ static int match_impl(const void *A, const void *B, int n, int dtype, const floa
         cudaEventElapsedTime(&stats->ms_total, ev[0], ev[3]);
         cudaEventElapsedTime(&stats->ms_fw, ev[1], ev[2]);
         cudaEventElapsedTime(&stats->ms_project, ev[2], ev[3]);
+        stats->ms_gemm = ms_gemm;
+        stats->gemm_launches = gemm_launches;
+        stats->ms_sinkhorn = ms_sk;
+        stats->ms_step = ms_step;
+        stats->launches = launches_so_far() - launches0;
     }
     return GOAT_OK;  // an uncertified projection still returns its (eps-optimal) assignment
 }
@@ -381,6 +426,11 @@ const char *goat_strerror(int status) {
 size_t goat_workspace_bytes(int n, int dtype_AB, int precision) {
     if (n < 1 || !valid_dtype(dtype_AB) || !valid_precision(precision)) return 0;
     return make_plan(n, dtype_AB, precision, NEED_FW).total;
+}
+
+size_t goat_workspace_bytes_host(int n, int dtype_AB, int precision) {
+    if (n < 1 || !valid_dtype(dtype_AB) || !valid_precision(precision)) return 0;
+    return make_plan(n, dtype_AB, precision, NEED_FW | NEED_HOSTCOPY).total;
 }
 
 int goat_match(const void *A, const void *B, int n, int dtype_AB, const float *init, float eps_rel, int max_iter,

@@ -400,6 +400,7 @@ static int rows_grid(int n, int cap_per_sm = 8) {
 }
 
 int adj_to_bf16(const void *A, int dtype, int n, __nv_bfloat16 *A16, int ld16, float *deg, cudaStream_t s) {
+    note_launches(1);
     const int grid = grid_for((long long)n * 32, 256, 16);
     if (dtype == GOAT_DTYPE_U8)
         k_adj_to_bf16<uint8_t><<<grid, 256, 0, s>>>((const uint8_t *)A, n, A16, ld16, deg);
@@ -409,6 +410,7 @@ int adj_to_bf16(const void *A, int dtype, int n, __nv_bfloat16 *A16, int ld16, f
 }
 
 int count_asym(const void *A, int dtype, int n, int *count_dev, cudaStream_t s) {
+    note_launches(1);
     dim3 grid((unsigned)ceil_div(n, 32), (unsigned)ceil_div(n, 32)), block(32, 8);
     if (dtype == GOAT_DTYPE_U8)
         k_count_asym<uint8_t><<<grid, block, 0, s>>>((const uint8_t *)A, n, count_dev);
@@ -418,14 +420,17 @@ int count_asym(const void *A, int dtype, int n, int *count_dev, cudaStream_t s) 
 }
 
 void f32_to_terms(const float *X, int n, long long ldx, __nv_bfloat16 *Xb, int ld16, int terms, cudaStream_t s) {
+    note_launches(1);
     k_f32_to_terms<<<grid_for((long long)n * (ld16 / 8)), 256, 0, s>>>(X, n, ldx, Xb, ld16, terms);
 }
 
 void barycenter(const float *dA, const float *dB, int n, float *G, float *P, DevState *st, cudaStream_t s) {
+    note_launches(1);
     k_barycenter<<<rows_grid(n), 256, 0, s>>>(dA, dB, n, G, P, st);
 }
 
 void absmax(const float *X, long long total, unsigned *out, cudaStream_t s) {
+    note_launches(1);
     k_absmax<<<grid_for(total), 256, 0, s>>>(X, total, out);
 }
 
@@ -433,6 +438,7 @@ int ls_blocks(int n) { return rows_grid(n, 4); }
 
 void line_search(const float *G, const float *GQ, const float *P, const __nv_bfloat16 *Qb, int ldq, int terms,
                  const float *Qf, int n, double *partial, DevState *st, cudaStream_t s) {
+    note_launches(2);
     const int nb = ls_blocks(n);
     k_ls_partial<<<nb, 256, 0, s>>>(G, GQ, P, Qb, ldq, terms, Qf, n, partial);
     k_ls_final<<<1, 32, 0, s>>>(partial, nb, n, st);
@@ -440,6 +446,7 @@ void line_search(const float *G, const float *GQ, const float *P, const __nv_bfl
 
 void fw_update(float *P, float *G, const float *GQ, const __nv_bfloat16 *Qb, int ldq, int terms, const float *Qf,
                int n, const DevState *st, float alpha_value, unsigned *gmax_out, cudaStream_t s) {
+    note_launches(1);
     k_fw_update<<<rows_grid(n), 256, 0, s>>>(P, G, GQ, Qb, ldq, terms, Qf, n, st, alpha_value, gmax_out);
 }
 
@@ -448,6 +455,8 @@ void fw_roll(DevState *st, cudaStream_t s) { k_fw_roll<<<1, 1, 0, s>>>(st); }
 int objective(const void *A, const void *B, int dtype, int n, const int32_t *perm, unsigned long long *isum,
               double *fsum, unsigned long long *nA, unsigned long long *nB, double *fA, double *fB, int *bad,
               cudaStream_t s) {
+    note_launches(3);
+    note_launches(1);
     const int grid = (int)std::min<long long>(n, 152LL * 8);
     const long long total = (long long)n * n;
     if (dtype == GOAT_DTYPE_U8) {

@@ -375,6 +375,7 @@ int gemm_xyT(const GemmCall &c, cudaStream_t stream) {
     const int tiles = p.tiles_m * p.tiles_n;
     const int grid = tiles < sm_count ? tiles : sm_count;
     k_gemm_xyT<<<grid, GEMM_THREADS, GEMM_SMEM_BYTES, stream>>>(mx, my, p);
+    note_launches(1);
     return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
 }
 

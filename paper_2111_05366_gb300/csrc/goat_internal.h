@@ -39,6 +39,10 @@ struct GemmCall {
 
 int gemm_xyT(const GemmCall &c, cudaStream_t stream);
 
+// Kernel launches issued by this host thread (every launch site reports here).
+void note_launches(int k);
+long long launches_so_far();
+
 // Byte layout of the scratch workspace for size n (all offsets 256-aligned).
 struct Workspace {
     size_t state;       // DevState

@@ -294,6 +294,7 @@ long long sinkhorn_partial_elems(int n) {
 // Queues one Sinkhorn iteration.
 static void sinkhorn_iteration(const float *G, int n, long long ld, float *f, float *g, double *partial,
                                DevState *st, int max_iter, const SinkhornLaunch &L, cudaStream_t s) {
+    note_launches(4);
     k_sk_row<<<L.row_grid, 256, 0, s>>>(G, n, ld, g, f, st);
     k_sk_colpart<<<dim3(L.colpart_x, L.colpart_y), 256, 0, s>>>(G, n, ld, f, g, partial, L.rows_per_chunk, st);
     k_sk_colfinal<<<L.final_grid, 256, 0, s>>>(partial, L.colpart_y, n, G, ld, f, g, st);
@@ -321,11 +322,13 @@ int sinkhorn_solve(const float *G, int n, long long ld, float *f, float *g, doub
 }
 
 void sinkhorn_begin(DevState *st, float eps, float tol, float *g_zero, int n, cudaStream_t s) {
+    note_launches(1);
     k_sk_begin<<<g_zero ? (int)std::min<int64_t>(ceil_div(n, 256), 1024) : 1, 256, 0, s>>>(st, eps, tol, g_zero, n);
 }
 
 void write_q(const float *G, int n, long long ld, const float *f, const float *g, const DevState *st,
              __nv_bfloat16 *Qb, int ldq, int terms, float *Qf, long long ldf, cudaStream_t s) {
+    note_launches(1);
     const long long total = (long long)n * (ldq / 8);
     const int grid = (int)std::min<long long>(ceil_div(total, 256), 152LL * 32);
     k_write_q<<<grid, 256, 0, s>>>(G, n, ld, f, g, st, Qb, ldq, terms, Qf, ldf);

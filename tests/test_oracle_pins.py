@@ -201,12 +201,17 @@ def test_log_and_scaling_domain_agree_with_warm_start():
     np.testing.assert_allclose(f1, f2, atol=1e-10 * eps)
     np.testing.assert_allclose(g1, g2, atol=1e-10 * eps)
     assert r1 == pytest.approx(r2, rel=1e-8, abs=1e-14)
-    # sampled-row/column forms agree with the full solve
+    # block-row / block-column forms agree with one full iteration
     rows = np.array([0, 7, 29])
-    fr = oracle.lot_rows(M.astype(np.float32), g0.astype(np.float32), eps, rows)
-    _, fl, _, _, _ = oracle.lot_log(M.astype(np.float32).astype(np.float64), eps, 0.0, 1,
-                                    g_init=g0.astype(np.float32).astype(np.float64))
+    M32, g32 = M.astype(np.float32), g0.astype(np.float32)
+    fr = oracle.lot_rows(M32[rows], g32, eps)
+    _, fl, gl, _, _ = oracle.lot_log(M32.astype(np.float64), eps, 0.0, 1, g_init=g32.astype(np.float64))
     np.testing.assert_allclose(fr, fl[rows], atol=1e-12 * eps)
+    # column sums of the row-scaled Q (before the column scaling) give g_new = g - eps log S
+    f32 = fl.astype(np.float32)
+    S = oracle.lot_colsums(M32[:, rows], f32, g32[rows], eps)
+    Sfull = np.exp((f32.astype(np.float64)[:, None] + g32.astype(np.float64)[None, :] - M32.astype(np.float64)) / eps).sum(0)
+    np.testing.assert_allclose(S, Sfull[rows], rtol=1e-12)
 
 
 def test_sinkhorn_small_eps_recovers_unique_lap_optimum():
