@@ -216,6 +216,28 @@ GOAT_API int goat_objective(const void *A, const void *B, int n, int dtype_AB, c
                    double *disagreements_out, void *workspace, size_t workspace_bytes, goat_stream_t stream);
 
 /*
+ * goat_sinkhorn_noalloc -- goat_sinkhorn for callers that cannot allocate.
+ * The paper has no counterpart: this exists for callers that must not allocate
+ * device memory during the call (they run under an allocator they do not own,
+ * inside a fixed memory budget, or on a thread that must not synchronise with the
+ * device the way cudaMalloc/cudaFree can).  It allocates nothing and never waits
+ * on the device: its scratch is one static device array of about 2 MiB, held by
+ * every GPU that loads the library until the process exits.
+ *   G, n, eps, tol, f_out, g_io  as in goat_sinkhorn; n <= 4096, larger n returns
+ *                                 GOAT_ERR_INVALID_ARG (the array is sized for 4096).
+ *   max_iter   iteration slots queued; once the residual falls below tol the
+ *              remaining slots do no work, so the result equals goat_sinkhorn's.
+ *   iters_out, resid_out  DEVICE int / float (nullable), written when the stream
+ *              reaches the end of the call.
+ * The first call on each device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array and each starts by clearing its state block, so calls
+ * that overlap on the GPU (other streams, other host threads) race: serialise them.
+ */
+GOAT_API int goat_sinkhorn_noalloc(const float *G, int n, float eps, float tol, int max_iter, float *f_out,
+                                   float *g_io, int *iters_out, float *resid_out, goat_stream_t stream);
+
+/*
  * goat_gemm_bf16_xyT -- kernel-level entry to the tensor-core product behind
  * goat_gradient (Alg. 3 step 1 evaluates grad f with two such products):
  *   out[r][c] = scale * sum_k X[r][k mod kx_period] * Y[c][k],  0 <= k < k_total.

@@ -86,6 +86,8 @@ long long sinkhorn_partial_elems(int n);
 void sinkhorn_begin(DevState *st, float eps, float tol, float *g_zero, int n, cudaStream_t s);
 int sinkhorn_solve(const float *G, int n, long long ld, float *f, float *g, double *partial, DevState *st,
                    int max_iter, int check_every, int *host_flag, cudaStream_t s);
+void sinkhorn_queue_fixed(const float *G, int n, long long ld, float *f, float *g, double *partial, DevState *st,
+                          int max_iter, cudaStream_t s);
 void write_q(const float *G, int n, long long ld, const float *f, const float *g, const DevState *st,
              __nv_bfloat16 *Qb, int ldq, int terms, float *Qf, long long ldf, cudaStream_t s);
 

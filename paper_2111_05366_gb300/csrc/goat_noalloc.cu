@@ -1,0 +1,108 @@
+// goat_noalloc.cu -- a Sinkhorn entry point that allocates nothing.
+//
+// Some callers cannot allocate device memory while they run this step: code
+// that runs under an allocator it does not own (a framework's caching
+// allocator, a real-time loop with a fixed memory budget, a host thread that
+// must not synchronise with the device as cudaMalloc/cudaFree can), or code
+// that has no way to hand us a workspace.  goat_sinkhorn_noalloc serves them: its
+// scratch (the device state block and the column partial sums) lives in one
+// file-scope device array that every GPU loading the library holds until exit,
+// and it neither allocates nor waits on the device.
+#include <cstring>
+#include <mutex>
+
+#include "goat_common.cuh"
+#include "goat_internal.h"
+
+namespace goat {
+
+// Largest n this entry point accepts; the scratch below is sized for it.
+constexpr int kNoallocMaxN = 4096;
+// DevState (rounded to 16 KiB) + at most ceil(n / 64) row chunks x n FP64 column partials.
+constexpr size_t kNoallocStateBytes = 16384;
+constexpr size_t kNoallocScratchBytes = kNoallocStateBytes + (size_t)(kNoallocMaxN / 64) * kNoallocMaxN * 8;
+
+static_assert(sizeof(DevState) <= kNoallocStateBytes, "state block does not fit its slot");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+// Address of g_noalloc_scratch on each device, looked up once per device with
+// that device current (the host-side symbol is a stand-in, not a device address).
+static unsigned char *noalloc_scratch_address(int *status) {
+    static std::mutex mu;
+    static unsigned char *addr[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        *status = GOAT_ERR_CUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            *status = GOAT_ERR_CUDA;
+            return nullptr;
+        }
+        addr[dev] = static_cast<unsigned char *>(p);
+    }
+    *status = GOAT_OK;
+    return addr[dev];
+}
+
+__global__ void k_noalloc_state_init(DevState *st) {
+    st->eps_rel = 0.03f;
+    st->maximize = 1;
+    st->eps = 1.0f;
+    st->c = 1.4426950408889634f;
+}
+
+__global__ void k_noalloc_report(const DevState *st, int *iters_out, float *resid_out) {
+    if (iters_out) *iters_out = st->sk_iters;
+    if (resid_out) *resid_out = st->sk_resid;
+}
+
+}  // namespace goat
+
+using namespace goat;
+
+extern "C" {
+
+int goat_sinkhorn_noalloc(const float *G, int n, float eps, float tol, int max_iter, float *f_out, float *g_io,
+                          int *iters_out, float *resid_out, goat_stream_t stream) {
+    if (!G || !f_out || !g_io || n < 1 || !(eps > 0.0f) || !(tol >= 0.0f) || max_iter < 1)
+        return GOAT_ERR_INVALID_ARG;
+    if (n > kNoallocMaxN) return GOAT_ERR_INVALID_ARG;  // beyond the static scratch
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return GOAT_ERR_CUDA;
+    }
+    if (major != 10 || minor != 3) return GOAT_ERR_UNSUPPORTED;
+    int status = GOAT_OK;
+    unsigned char *scratch = noalloc_scratch_address(&status);
+    if (!scratch) return status;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevState *st = reinterpret_cast<DevState *>(scratch);
+    double *partial = reinterpret_cast<double *>(scratch + kNoallocStateBytes);
+    // the array keeps the previous call's contents: the state block must start at zero
+    // (the partial sums are fully rewritten by every iteration before they are read)
+    if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) {
+        cudaGetLastError();
+        return GOAT_ERR_CUDA;
+    }
+    k_noalloc_state_init<<<1, 1, 0, s>>>(st);
+    note_launches(1);
+    sinkhorn_begin(st, eps, tol, nullptr, n, s);
+    sinkhorn_queue_fixed(G, n, n, f_out, g_io, partial, st, max_iter, s);
+    k_noalloc_report<<<1, 1, 0, s>>>(st, iters_out, resid_out);
+    note_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -321,6 +321,14 @@ int sinkhorn_solve(const float *G, int n, long long ld, float *f, float *g, doub
     return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
 }
 
+// Queues exactly max_iter iteration slots without any host synchronisation; the
+// kernels stop doing work once the device stop flag rises.
+void sinkhorn_queue_fixed(const float *G, int n, long long ld, float *f, float *g, double *partial, DevState *st,
+                          int max_iter, cudaStream_t s) {
+    const SinkhornLaunch L = sinkhorn_launch(n);
+    for (int t = 0; t < max_iter; ++t) sinkhorn_iteration(G, n, ld, f, g, partial, st, max_iter, L, s);
+}
+
 void sinkhorn_begin(DevState *st, float eps, float tol, float *g_zero, int n, cudaStream_t s) {
     note_launches(1);
     k_sk_begin<<<g_zero ? (int)std::min<int64_t>(ceil_div(n, 256), 1024) : 1, 256, 0, s>>>(st, eps, tol, g_zero, n);
