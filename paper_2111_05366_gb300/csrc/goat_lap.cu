@@ -293,8 +293,13 @@ __global__ void __launch_bounds__(1024) k_lap_fill(const float *__restrict__ M, 
                     s_b[0] = s_b[w];
                     s_j[0] = s_j[w];
                 }
-            L.owner[s_j[0]] = i;
-            L.assign[i] = s_j[0];
+            const int j = s_j[0];
+            if (j >= 0 && j < n) {
+                L.owner[j] = i;
+                L.assign[i] = j;
+            } else if (!st->error) {
+                st->error = GOAT_ERR_NOT_CONVERGED;  // no free object left: inconsistent state, skip
+            }
         }
         __syncthreads();
     }
@@ -316,7 +321,7 @@ __global__ void __launch_bounds__(256) k_lap_gap(const float *__restrict__ M, in
         top2_warp(b1, b2, j1);
         if (lane == 0) {
             const int j = L.assign[i];
-            acc += (double)(b1 - (benefit(Mi[j], q) - L.price[j]));
+            if (j >= 0 && j < n) acc += (double)(b1 - (benefit(Mi[j], q) - L.price[j]));
         }
     }
     if (lane == 0 && acc != 0.0) atomicAdd(out, acc);
@@ -328,7 +333,8 @@ __global__ void k_assignment_cost(const float *__restrict__ M, int n, const int 
     double acc = 0.0;
     for (int base = 0; base < n; base += 1024) {
         const int i = base + threadIdx.x;
-        buf[threadIdx.x] = (i < n) ? (double)M[(long long)i * n + perm[i]] : 0.0;
+        const int pi = (i < n) ? perm[i] : -1;
+        buf[threadIdx.x] = (pi >= 0 && pi < n) ? (double)M[(long long)i * n + pi] : 0.0;
         __syncthreads();
         if (threadIdx.x == 0) {
             const int lim = min(1024, n - base);
