@@ -60,7 +60,10 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel-case", choices=["gemm", "sinkhorn", "lap"], default=None,
+    ap.add_argument("--pairs", type=int, default=512)
+    ap.add_argument("--restarts", type=int, default=20)
+    ap.add_argument("--train-pairs", type=int, default=48)
+    ap.add_argument("--kernel-case", choices=["gemm", "sinkhorn", "lap", "batched", "warmstart"], default=None,
                     help="run only one step kind a few times on the workload (the small cases profiled with ncu)")
     ap.add_argument("--repeat", type=int, default=3)
     return ap.parse_args()
@@ -241,6 +244,10 @@ def run_kernel_case(args):
     from paper_2111_05366_gb300 import synthetic
     torch.cuda.set_device(0)
     goat.load()
+    if args.kernel_case == "batched":
+        return run_batched_case(args)
+    if args.kernel_case == "warmstart":
+        return run_warmstart_case(args)
     n = args.n
     gp = synthetic.large_sbm_pair(n, seed=args.seed)
     A = torch.from_numpy(gp.A).cuda()
@@ -277,6 +284,102 @@ def run_kernel_case(args):
         out["cost"], out["gap"] = cost, gap
     torch.cuda.synchronize()
     out["ms_per_call"] = e0.elapsed_time(e1) / args.repeat
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_warmstart_case(args):
+    """The learned warm start: train the network on converged duals of GOAT runs on
+    --train-pairs correlated ER / SBM pairs (n in [500, 2000], half weighted), then
+    compare Sinkhorn to marginal tol 1e-4 from the network's duals against a cold
+    start on a weighted correlated ER pair, n = --n (8192), p = 0.05, rho = 0.8,
+    lognormal(0, 1) weights, at the barycenter gradient and two FW steps later."""
+    import torch
+
+    import paper_2111_05366_gb300 as goat
+    from paper_2111_05366_gb300 import synthetic, warmstart
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    log("collecting converged duals")
+    t0 = time.time()
+    X, T = warmstart.collect(warmstart.default_training_pairs(args.train_pairs, seed=args.seed), fw_steps=3)
+    t_collect = time.time() - t0
+    log(f"{X.shape[0]} samples; training")
+    e0.record()
+    master, adam, wb, losses = warmstart.train(X, T, steps=3000, batch=16384, lr=3e-3, seed=0)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_train = e0.elapsed_time(e1)
+    gp = synthetic.rho_er_pair(args.n, 0.05, 0.8, seed=args.seed + 5, weighted=True)
+    A, B = torch.from_numpy(gp.A).cuda(), torch.from_numpy(gp.B).cuda()
+    n = gp.n
+    P = torch.full((n, n), 1.0 / n, dtype=torch.float32, device="cuda")
+    G = goat.goat_gradient(A, B, P, precision=goat.GOAT_PREC_FP32)
+    rows = []
+    for step in range(3):
+        eps = 0.03 * float(G.abs().max())
+        e0.record()
+        f, g, Q, it_c, r_c = goat.goat_sinkhorn(G, eps, 1e-4, 5000, want_Q=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_c = e0.elapsed_time(e1)
+        e0.record()
+        g0 = goat.goat_mlp_warm_start(G, A, B, eps, wb)
+        _, _, _, it_w, r_w = goat.goat_sinkhorn(G, eps, 1e-4, 5000, g_init=g0)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_w = e0.elapsed_time(e1)
+        rows.append({"fw_step": step, "cold_iters": it_c, "warm_iters": it_w, "cold_ms": ms_c,
+                     "warm_ms_incl_features_and_mlp": ms_w, "cold_resid": r_c, "warm_resid": r_w})
+        GQ = goat.goat_gradient(A, B, Q, precision=goat.GOAT_PREC_FP32)
+        alpha, _, _ = goat.goat_line_search(G, GQ, P, Q)
+        goat.goat_fw_update(P, G, Q, GQ, alpha)
+    out = {"case": "warmstart", "n": n, "train_samples": int(X.shape[0]), "train_pairs": args.train_pairs,
+           "collect_s": t_collect, "train_ms_3000_steps": ms_train, "loss_first": losses[0], "loss_last": losses[-1],
+           "eval": rows}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_batched_case(args):
+    """The batched workload: --pairs correlated ER pairs with n ~ U{50..1000},
+    p ~ U[0.02, 0.2], rho ~ U[0.6, 1.0], each from --restarts starts (restart 0 the
+    barycenter, the others (J + K)/2 random starts), one CUDA-graph replay per FW
+    iteration.  Reports solved pairs per second and the mean matching accuracy."""
+    import torch
+
+    import paper_2111_05366_gb300 as goat
+    from paper_2111_05366_gb300 import synthetic
+    rng = np.random.default_rng(args.seed)
+    ns = rng.integers(50, 1001, size=args.pairs)
+    ps = rng.uniform(0.02, 0.2, size=args.pairs)
+    rhos = rng.uniform(0.6, 1.0, size=args.pairs)
+    log(f"generating {args.pairs} pairs")
+    gps = [synthetic.rho_er_pair(int(n), float(p), float(r), seed=args.seed + 17 * k)
+           for k, (n, p, r) in enumerate(zip(ns, ps, rhos))]
+    nn = np.array([g.n for g in gps], dtype=np.int32)
+    off = np.zeros(len(gps), dtype=np.int64)
+    off[1:] = np.cumsum(nn.astype(np.int64) ** 2)[:-1]
+    Ad = torch.from_numpy(np.concatenate([g.A.ravel() for g in gps])).cuda()
+    Bd = torch.from_numpy(np.concatenate([g.B.ravel() for g in gps])).cuda()
+    prm = goat.default_params(sk_tol=args.sk_tol, sk_max_iter=args.sk_max_iter)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    log("first call (autotunes the Sinkhorn launch shape)")
+    goat.goat_match_batched(None, None, restarts=args.restarts, seed=args.seed, max_iter=args.max_iter,
+                            tol=args.fw_tol, params=prm, device_AB=(Ad, Bd, off, nn))
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.repeat):
+        perms, obj, best, its = goat.goat_match_batched(None, None, restarts=args.restarts, seed=args.seed,
+                                                        max_iter=args.max_iter, tol=args.fw_tol, params=prm,
+                                                        device_AB=(Ad, Bd, off, nn))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.repeat
+    acc = float(np.mean([(perms[k] == gps[k].truth).mean() for k in range(len(gps))]))
+    out = {"case": "batched", "pairs": args.pairs, "restarts": args.restarts,
+           "problems": args.pairs * args.restarts, "ms_per_batch": ms,
+           "pairs_per_s": args.pairs / (ms / 1000.0), "mean_accuracy": acc,
+           "mean_fw_iters_best": float(np.mean(its)), "sum_n3": float(np.sum(nn.astype(np.float64) ** 3))}
     print(json.dumps(out), flush=True)
     return 0
 

@@ -83,6 +83,9 @@ enum {
 
 #define GOAT_TRACE_MAX 256
 
+/* Parameters of the warm-start network (W1 [64][8], b1 [64], w2 [64], b2). */
+#define GOAT_MLP_PARAMS 641
+
 typedef struct goat_params {
     int precision;        /* GOAT_PREC_*, default GOAT_PREC_BF16                          */
     int sk_max_iter;      /* Sinkhorn iterations per Frank-Wolfe step, default 500        */
@@ -92,6 +95,10 @@ typedef struct goat_params {
     int project_on_grad;  /* 0: final LAP on P (default); 1: on grad f(P) (the paper's Alg. 3 line) */
     int lap_max_rounds;   /* cap on auction bidding rounds over all phases, default 1<<20 */
     int profile;          /* 1: time the phases with CUDA events on `stream` (stats ms_*), default 0 */
+    /* Learned warm start (device, GOAT_MLP_PARAMS BF16 values, or NULL): the first
+     * Sinkhorn solve of goat_match starts from the duals the network predicts; if
+     * that solve fails to reach sk_tol it is redone from a cold start. */
+    const void *mlp_weights;
 } goat_params;
 
 typedef struct goat_stats {
@@ -216,6 +223,34 @@ GOAT_API int goat_objective(const void *A, const void *B, int n, int dtype_AB, c
                    double *disagreements_out, void *workspace, size_t workspace_bytes, goat_stream_t stream);
 
 /*
+ * goat_match_batched -- many GOAT solves (Alg. 3) advanced together: num_pairs
+ * graph pairs of sizes n[p] (1 <= n[p] <= 2048), each solved from `restarts`
+ * starting points (Sec. 3.4): restart 0 is the barycenter J, restart r >= 1 the
+ * random start (J + K)/2 where K is the Sinkhorn-Knopp scaling of noise
+ * U_ij in (0, 1]: U_ij = (SplitMix64 output number ((q << 32) | (i n + j)) of the
+ * generator seeded with `seed`, shifted right by 40, plus 1) / 2^24, q the problem
+ * index pair * restarts + restart.  The best restart (largest objective, lowest
+ * index on ties) is returned per pair.  Each Frank-Wolfe iteration of all
+ * problems is one replay of a CUDA graph; the Sinkhorn launch shape is chosen per
+ * batch by timing candidates on the batch (cached per process).
+ *   A, B       device uint8, the pairs' symmetric 0/1 matrices packed back to back;
+ *              pair p is n[p] x n[p] row-major at byte offset adj_off[p] (HOST array).
+ *   n          HOST int[num_pairs].
+ *   perm_out   HOST int32[sum n[p]]: the pairs' best permutations, concatenated.
+ *   objective_out, best_restart, fw_iters_out  HOST [num_pairs] (nullable).
+ *   relaxed_out  DEVICE float (nullable): the final relaxed P of every problem (the
+ *              doubly stochastic "soft matching"), problems in order q, each n x n row-major.
+ *   params     precision must be GOAT_PREC_BF16; the Sinkhorn and FW limits apply per problem.
+ * Workspace: goat_workspace_bytes_batched(n, num_pairs, restarts) bytes, or NULL.
+ */
+GOAT_API size_t goat_workspace_bytes_batched(const int *n, int num_pairs, int restarts);
+GOAT_API int goat_match_batched(const void *A, const void *B, const long long *adj_off, const int *n, int num_pairs,
+                                int restarts, unsigned long long seed, float eps_rel, int max_iter, float tol,
+                                const goat_params *params, int32_t *perm_out, double *objective_out,
+                                int *best_restart, int *fw_iters_out, float *relaxed_out, void *workspace,
+                                size_t workspace_bytes, goat_stream_t stream);
+
+/*
  * goat_sinkhorn_noalloc -- goat_sinkhorn for callers that cannot allocate.
  * The paper has no counterpart: this exists for callers that must not allocate
  * device memory during the call (they run under an allocator they do not own,
@@ -236,6 +271,36 @@ GOAT_API int goat_objective(const void *A, const void *B, int n, int dtype_AB, c
  */
 GOAT_API int goat_sinkhorn_noalloc(const float *G, int n, float eps, float tol, int max_iter, float *f_out,
                                    float *g_io, int *iters_out, float *resid_out, goat_stream_t stream);
+
+/*
+ * Learned Sinkhorn warm start.  The paper has no counterpart; it serves Alg. 2:
+ * a small network predicts the LOT duals from per-node features so each solve
+ * starts close to its fixed point.  Nodes 0..n-1 are the rows of G (dual f),
+ * n..2n-1 its columns (dual g).
+ *
+ * goat_dual_features -- feats (device, 2n x 8 float): degree / mean degree,
+ *   2-hop degree / its mean, mean, max, std, min of the node's line of G over eps,
+ *   side (0 rows, 1 columns), ln(n) / 10.  A, B as in goat_match.
+ * goat_mlp_forward -- y = w2 . tanh(W1 x + b1) + b2 for N feature rows (device),
+ *   weights in BF16 (device, GOAT_MLP_PARAMS).  y is the dual over eps, each side's
+ *   mean removed.
+ * goat_mlp_train_step -- one mean-squared-error step on (x, t): grad_out (device,
+ *   GOAT_MLP_PARAMS floats) receives the gradient at the BF16 weights, loss_out
+ *   (device float) the loss; with lr > 0 an Adam step (Kingma & Ba, beta 0.9 /
+ *   0.999) updates the FP32 master weights, adam_state (2 x GOAT_MLP_PARAMS
+ *   floats: first, second moments) and the BF16 copy.  step counts from 1.
+ * goat_mlp_warm_start -- g_out (device, n floats) = eps * predicted g, the warm
+ *   start goat_sinkhorn takes in g_io.
+ */
+GOAT_API int goat_dual_features(const float *G, const void *A, const void *B, int n, int dtype_AB, float eps,
+                                float *feats, void *workspace, size_t workspace_bytes, goat_stream_t stream);
+GOAT_API int goat_mlp_forward(const void *weights_bf16, const float *x, int N, float *y, goat_stream_t stream);
+GOAT_API int goat_mlp_train_step(float *master, float *adam_state, void *weights_bf16, const float *x,
+                                 const float *t, int N, float lr, int step, float *loss_out, float *grad_out,
+                                 goat_stream_t stream);
+GOAT_API int goat_mlp_warm_start(const float *G, const void *A, const void *B, int n, int dtype_AB, float eps,
+                                 const void *weights_bf16, float *g_out, void *workspace, size_t workspace_bytes,
+                                 goat_stream_t stream);
 
 /*
  * goat_gemm_bf16_xyT -- kernel-level entry to the tensor-core product behind

@@ -75,6 +75,10 @@ def _load():
             "oracle_assignment_cost_f32": (ctypes.c_double, [_fp, ctypes.c_int, _ip]),
             "oracle_lap_certificate_f32": (None, [_fp, ctypes.c_int, _ip, _dp, _dp, _dp, _dp]),
             "oracle_brute_lap": (ctypes.c_double, [_dp, ctypes.c_int, ctypes.c_int, _ip, _ip]),
+            "oracle_random_start": (None, [ctypes.c_int, ctypes.c_uint64, ctypes.c_int, _dp]),
+            "oracle_splitmix64_output": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint64]),
+            "oracle_dual_features": (None, [_dp, _dp, _dp, ctypes.c_int, ctypes.c_double, _dp]),
+            "oracle_mlp_loss_grad": (ctypes.c_double, [_dp, _dp, _dp, ctypes.c_int, _dp, _dp]),
             "oracle_brute_qap": (ctypes.c_double, [_dp, _dp, ctypes.c_int, ctypes.c_int, _ip]),
             "oracle_goat": (ctypes.c_int, [_dp, _dp, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_int,
                                            ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -278,6 +282,18 @@ def lap_certificate(C, perm, u, v):
     return mv.value, gap.value
 
 
+def splitmix64(seed: int, k: int) -> int:
+    """Output number k of SplitMix64 seeded with `seed` (counter form)."""
+    return int(_load().oracle_splitmix64_output(seed, k))
+
+
+def random_start(n: int, seed: int, q: int) -> np.ndarray:
+    """The paper's random start (J + K)/2 (Sec. 3.4), K = Sinkhorn-Knopp of SplitMix64 noise."""
+    out = np.empty((n, n))
+    _load().oracle_random_start(n, seed, q, _ptr(out, _dp))
+    return out
+
+
 def brute_lap(C, maximize: bool = True):
     """Exhaustive LAP over all n! permutations (n <= 10). Returns (cost, perm, n_optimal)."""
     C = _d(C)
@@ -326,3 +342,23 @@ def goat(A, B, P0=None, eps_rel: float = 0.03, max_iter: int = 30, tol: float = 
 def faq(A, B, **kw):
     """FAQ (Alg. 1): GOAT with the Hungarian LAP as the direction step."""
     return goat(A, B, use_lap=True, **kw)
+
+
+def dual_features(G, A, B, eps: float) -> np.ndarray:
+    """Per-node features of the learned warm start (2n x 8), from their definitions."""
+    G, A, B = _d(G), _d(A), _d(B)
+    n = _square(G, A, B)
+    out = np.empty((2 * n, 8))
+    _load().oracle_dual_features(_ptr(G, _dp), _ptr(A, _dp), _ptr(B, _dp), n, eps, _ptr(out, _dp))
+    return out
+
+
+def mlp_loss_grad(params, x, t):
+    """(loss, gradient[641], outputs) of the warm-start network's mean squared error, FP64."""
+    params, x, t = _d(params), _d(x), _d(t)
+    N = x.shape[0]
+    grad = np.empty(641)
+    y = np.empty(N)
+    L = _load().oracle_mlp_loss_grad(_ptr(params, _dp), _ptr(x, _dp), _ptr(t, _dp), N, _ptr(grad, _dp),
+                                     _ptr(y, _dp))
+    return L, grad, y

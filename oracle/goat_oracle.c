@@ -528,6 +528,120 @@ void oracle_lap_certificate_f32(const float *C, int n, const int *perm, const do
 }
 
 /* ------------------------------------------------------------------ */
+/* random starting points (Sec. 3.4)                                    */
+/* ------------------------------------------------------------------ */
+
+/* SplitMix64 (Steele, Lea, Flood 2014): the k-th output of the generator
+ * seeded with `seed` is the mix of seed + (k + 1) * 0x9E3779B97F4A7C15. */
+uint64_t oracle_splitmix64_output(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + (k + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* The paper's random start P0 = (J + K) / 2, J = 11^T / n, with K the
+ * Sinkhorn-Knopp scaling of the noise U_ij = ((output k >> 40) + 1) / 2^24,
+ * k = (q << 32) | (i n + j), for problem q. */
+void oracle_random_start(int n, uint64_t seed, int q, double *P0)
+{
+    double *U = alloc_mat(n), *K = alloc_mat(n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            uint64_t k = ((uint64_t)q << 32) | (uint64_t)((uint32_t)i * (uint32_t)n + (uint32_t)j);
+            U[IDX(i, j, n)] = (double)((oracle_splitmix64_output(seed, k) >> 40) + 1u) / 16777216.0;
+        }
+    oracle_sinkhorn_knopp(U, n, 1e-12, 100000, NULL, K, NULL, NULL, NULL);
+    for (size_t t = 0; t < (size_t)n * (size_t)n; ++t) P0[t] = 0.5 / (double)n + 0.5 * K[t];
+    free(U); free(K);
+}
+
+/* ------------------------------------------------------------------ */
+/* learned warm start: node features and the network (no counterpart in */
+/* the paper; written from their definitions)                           */
+/* ------------------------------------------------------------------ */
+
+static void line_stats(const double *x, int n, int stride, double scale, double *mean, double *mx, double *sd,
+                       double *mn)
+{
+    double s = 0.0, s2 = 0.0, hi = -INFINITY, lo = INFINITY;
+    for (int k = 0; k < n; ++k) {
+        double v = x[(size_t)k * (size_t)stride] * scale;
+        s += v;
+        s2 += v * v;
+        if (v > hi) hi = v;
+        if (v < lo) lo = v;
+    }
+    *mean = s / n;
+    double var = s2 / n - (*mean) * (*mean);
+    *sd = var > 0.0 ? sqrt(var) : 0.0;
+    *mx = hi;
+    *mn = lo;
+}
+
+/* feats (2n x 8): nodes 0..n-1 are the rows of G, n..2n-1 its columns:
+ * degree / mean degree, 2-hop degree / its mean, mean, max, std, min of the
+ * node's line of G over eps, side, ln(n)/10. */
+void oracle_dual_features(const double *G, const double *A, const double *B, int n, double eps, double *feats)
+{
+    double *deg = (double *)calloc(2 * (size_t)n, sizeof(double));
+    double *hop = (double *)calloc(2 * (size_t)n, sizeof(double));
+    double sdA = 0, sdB = 0, shA = 0, shB = 0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) { deg[i] += A[IDX(i, j, n)]; deg[n + i] += B[IDX(i, j, n)]; }
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) { hop[i] += A[IDX(i, k, n)] * deg[k]; hop[n + i] += B[IDX(i, k, n)] * deg[n + k]; }
+    for (int i = 0; i < n; ++i) { sdA += deg[i]; sdB += deg[n + i]; shA += hop[i]; shB += hop[n + i]; }
+    for (int v = 0; v < 2 * n; ++v) {
+        int side = v >= n, idx = side ? v - n : v;
+        double *o = feats + (size_t)v * 8;
+        double md = (side ? sdB : sdA) / n, mh = (side ? shB : shA) / n;
+        o[0] = md > 0 ? deg[v] / md : 0.0;
+        o[1] = mh > 0 ? hop[v] / mh : 0.0;
+        if (!side) line_stats(G + IDX(idx, 0, n), n, 1, 1.0 / eps, &o[2], &o[3], &o[4], &o[5]);
+        else line_stats(G + idx, n, n, 1.0 / eps, &o[2], &o[3], &o[4], &o[5]);
+        o[6] = side;
+        o[7] = log((double)n) / 10.0;
+    }
+    free(deg); free(hop);
+}
+
+/* The warm-start network y = w2 . tanh(W1 x + b1) + b2 (hidden width 64, 8
+ * inputs; packed parameters W1 [64][8] at 0, b1 at 512, w2 at 576, b2 at 640)
+ * and the mean squared error L = (1/N) sum_s (y_s - t_s)^2 with its gradient
+ * by the chain rule.  y_out (nullable) gets the outputs.  Returns L. */
+double oracle_mlp_loss_grad(const double *prm, const double *x, const double *t, int N, double *grad, double *y_out)
+{
+    double L = 0.0;
+    if (grad) memset(grad, 0, sizeof(double) * 641);
+    for (int s = 0; s < N; ++s) {
+        const double *xs = x + (size_t)s * 8;
+        double h[64], y = prm[640];
+        for (int k = 0; k < 64; ++k) {
+            double z = prm[512 + k];
+            for (int d = 0; d < 8; ++d) z += prm[k * 8 + d] * xs[d];
+            h[k] = tanh(z);
+            y += prm[576 + k] * h[k];
+        }
+        if (y_out) y_out[s] = y;
+        double e = y - t[s];
+        L += e * e / N;
+        if (grad) {
+            double dy = 2.0 * e / N;
+            grad[640] += dy;
+            for (int k = 0; k < 64; ++k) {
+                grad[576 + k] += dy * h[k];
+                double dz = dy * prm[576 + k] * (1.0 - h[k] * h[k]);
+                grad[512 + k] += dz;
+                for (int d = 0; d < 8; ++d) grad[k * 8 + d] += dz * xs[d];
+            }
+        }
+    }
+    return L;
+}
+
+/* ------------------------------------------------------------------ */
 /* brute force over all n! permutations (n <= 10)                       */
 /* ------------------------------------------------------------------ */
 

@@ -33,11 +33,14 @@ GOAT_DTYPE_F32 = 1
 GOAT_PREC_BF16 = 0
 GOAT_PREC_FP32 = 1
 GOAT_TRACE_MAX = 256
+GOAT_MLP_PARAMS = 641
 
 EXPORTED = ["goat_default_params", "goat_strerror", "goat_workspace_bytes", "goat_workspace_bytes_host",
             "goat_match", "goat_match_host",
             "goat_gradient", "goat_sinkhorn", "goat_line_search", "goat_fw_update", "goat_project",
-            "goat_objective", "goat_gemm_bf16_xyT", "goat_sinkhorn_noalloc"]
+            "goat_objective", "goat_gemm_bf16_xyT", "goat_sinkhorn_noalloc", "goat_match_batched",
+            "goat_workspace_bytes_batched", "goat_dual_features", "goat_mlp_forward", "goat_mlp_train_step",
+            "goat_mlp_warm_start"]
 
 
 class GoatError(RuntimeError):
@@ -49,7 +52,8 @@ class GoatError(RuntimeError):
 class goat_params(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("sk_max_iter", ctypes.c_int), ("sk_tol", ctypes.c_float),
                 ("sk_warm_start", ctypes.c_int), ("sk_check_every", ctypes.c_int),
-                ("project_on_grad", ctypes.c_int), ("lap_max_rounds", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("project_on_grad", ctypes.c_int), ("lap_max_rounds", ctypes.c_int), ("profile", ctypes.c_int),
+                ("mlp_weights", ctypes.c_void_p)]
 
 
 class goat_stats(ctypes.Structure):
@@ -101,6 +105,14 @@ def load():
                                     ctypes.c_size_t, _vp]),
             "goat_gemm_bf16_xyT": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _i, _f, _vp, _i, _i, _i, _vp]),
             "goat_sinkhorn_noalloc": (_i, [_vp, _i, _f, _f, _i, _vp, _vp, _vp, _vp, _vp]),
+            "goat_workspace_bytes_batched": (ctypes.c_size_t, [_vp, _i, _i]),
+            "goat_dual_features": (_i, [_vp, _vp, _vp, _i, _i, _f, _vp, _vp, ctypes.c_size_t, _vp]),
+            "goat_mlp_forward": (_i, [_vp, _vp, _i, _vp, _vp]),
+            "goat_mlp_train_step": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _f, _i, _vp, _vp, _vp]),
+            "goat_mlp_warm_start": (_i, [_vp, _vp, _vp, _i, _i, _f, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+            "goat_match_batched": (_i, [_vp, _vp, _vp, _vp, _i, _i, ctypes.c_ulonglong, _f, _i, _f,
+                                        ctypes.POINTER(goat_params), _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t,
+                                        _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -160,6 +172,8 @@ def default_params(**overrides) -> goat_params:
     for k, v in overrides.items():
         if not hasattr(p, k):
             raise KeyError(k)
+        if k == "mlp_weights" and v is not None and not isinstance(v, int):
+            v = _dev(v, _torch().bfloat16, (GOAT_MLP_PARAMS,), "mlp_weights").value
         setattr(p, k, v)
     return p
 
@@ -357,3 +371,113 @@ def goat_sinkhorn_noalloc(G, eps: float, tol: float, max_iter: int, g_init=None)
                                      _stream())
     _check(r, "goat_sinkhorn_noalloc")
     return f, g, it, res
+
+
+BATCH_MAX_N = 2048
+
+
+def goat_match_batched(As, Bs, restarts: int = 1, seed: int = 0, eps_rel: float = 0.03, max_iter: int = 30,
+                       tol: float = 0.03, params: goat_params | None = None, device_AB=None, want_relaxed=False):
+    """Batched GOAT: lists of uint8 numpy matrices (pairs of uneven n), `restarts` starts each.
+
+    The pairs are packed into one device buffer here (marshalling); all arithmetic
+    runs in libgoat.  `device_AB` may pass an already packed (A, B, adj_off, n)
+    tuple of device tensors / host arrays to keep the copy out of a timed region.
+    Returns (list of perms, objectives, best restarts, FW iterations), plus the list of
+    every problem's final relaxed P (problem order pair * restarts + restart) when
+    want_relaxed is set."""
+    torch = _torch()
+    if device_AB is None:
+        ns = np.array([a.shape[0] for a in As], dtype=np.int32)
+        off = np.zeros(len(As), dtype=np.int64)
+        off[1:] = np.cumsum(ns.astype(np.int64) ** 2)[:-1]
+        Ah = np.concatenate([np.ascontiguousarray(a, dtype=np.uint8).ravel() for a in As])
+        Bh = np.concatenate([np.ascontiguousarray(b_, dtype=np.uint8).ravel() for b_ in Bs])
+        Ad = torch.from_numpy(Ah).cuda()
+        Bd = torch.from_numpy(Bh).cuda()
+    else:
+        Ad, Bd, off, ns = device_AB
+    num = len(ns)
+    perm = np.empty(int(ns.sum()), dtype=np.int32)
+    obj = np.empty(num, dtype=np.float64)
+    best = np.empty(num, dtype=np.int32)
+    its = np.empty(num, dtype=np.int32)
+    p = params if params is not None else default_params()
+    rel = None
+    if want_relaxed:
+        rel = torch.empty(int((ns.astype(np.int64) ** 2).sum()) * restarts, dtype=torch.float32, device=Ad.device)
+    r = load().goat_match_batched(_dev(Ad, torch.uint8, None, "A"), _dev(Bd, torch.uint8, None, "B"),
+                                  off.ctypes.data_as(ctypes.c_void_p), ns.ctypes.data_as(ctypes.c_void_p), num,
+                                  int(restarts), ctypes.c_ulonglong(seed), float(eps_rel), int(max_iter),
+                                  float(tol), ctypes.byref(p), perm.ctypes.data_as(ctypes.c_void_p),
+                                  obj.ctypes.data_as(ctypes.c_void_p), best.ctypes.data_as(ctypes.c_void_p),
+                                  its.ctypes.data_as(ctypes.c_void_p),
+                                  _dev(rel, torch.float32, None, "relaxed") if rel is not None else None, None, 0,
+                                  _stream())
+    _check(r, "goat_match_batched")
+    cuts = np.cumsum(ns)[:-1]
+    out = (np.split(perm, cuts), obj, best, its)
+    if want_relaxed:
+        mats, o = [], 0
+        relh = rel.cpu().numpy()
+        for k in range(num):
+            for _ in range(restarts):
+                m = int(ns[k]) ** 2
+                mats.append(relh[o:o + m].reshape(int(ns[k]), int(ns[k])))
+                o += m
+        out = out + (mats,)
+    return out
+
+
+# ---------------------------------------------------------------- learned warm start
+
+def goat_dual_features(G, A, B, eps: float):
+    """Per-node features (2n x 8 float32 tensor) of the learned Sinkhorn warm start."""
+    torch = _torch()
+    n = G.shape[0]
+    F = torch.empty((2 * n, 8), dtype=torch.float32, device=G.device)
+    r = load().goat_dual_features(_dev(G, torch.float32, (n, n), "G"), _dev(A, A.dtype, (n, n), "A"),
+                                  _dev(B, A.dtype, (n, n), "B"), n, _adj_dtype(A), float(eps),
+                                  _dev(F, torch.float32, (2 * n, 8), "feats"), None, 0, _stream())
+    _check(r, "goat_dual_features")
+    return F
+
+
+def goat_mlp_forward(weights_bf16, x):
+    """Network outputs for feature rows x (N x 8): predicted duals over eps."""
+    torch = _torch()
+    N = x.shape[0]
+    y = torch.empty(N, dtype=torch.float32, device=x.device)
+    r = load().goat_mlp_forward(_dev(weights_bf16, torch.bfloat16, (GOAT_MLP_PARAMS,), "weights"),
+                                _dev(x, torch.float32, (N, 8), "x"), N, _dev(y, torch.float32, (N,), "y"), _stream())
+    _check(r, "goat_mlp_forward")
+    return y
+
+
+def goat_mlp_train_step(master, adam_state, weights_bf16, x, t, lr: float, step: int, grad=None, loss=None):
+    """One training step (loss, gradient at the BF16 weights, Adam update when lr > 0)."""
+    torch = _torch()
+    N = x.shape[0]
+    grad = grad if grad is not None else torch.empty(GOAT_MLP_PARAMS, dtype=torch.float32, device=x.device)
+    loss = loss if loss is not None else torch.empty(1, dtype=torch.float32, device=x.device)
+    r = load().goat_mlp_train_step(_dev(master, torch.float32, (GOAT_MLP_PARAMS,), "master"),
+                                   _dev(adam_state, torch.float32, (2 * GOAT_MLP_PARAMS,), "adam_state"),
+                                   _dev(weights_bf16, torch.bfloat16, (GOAT_MLP_PARAMS,), "weights"),
+                                   _dev(x, torch.float32, (N, 8), "x"), _dev(t, torch.float32, (N,), "t"), N,
+                                   float(lr), int(step), _dev(loss, torch.float32, (1,), "loss"),
+                                   _dev(grad, torch.float32, (GOAT_MLP_PARAMS,), "grad"), _stream())
+    _check(r, "goat_mlp_train_step")
+    return loss, grad
+
+
+def goat_mlp_warm_start(G, A, B, eps: float, weights_bf16):
+    """Warm-start column duals g (n, float32) predicted by the network for goat_sinkhorn."""
+    torch = _torch()
+    n = G.shape[0]
+    g = torch.empty(n, dtype=torch.float32, device=G.device)
+    r = load().goat_mlp_warm_start(_dev(G, torch.float32, (n, n), "G"), _dev(A, A.dtype, (n, n), "A"),
+                                   _dev(B, A.dtype, (n, n), "B"), n, _adj_dtype(A), float(eps),
+                                   _dev(weights_bf16, torch.bfloat16, (GOAT_MLP_PARAMS,), "weights"),
+                                   _dev(g, torch.float32, (n,), "g"), None, 0, _stream())
+    _check(r, "goat_mlp_warm_start")
+    return g

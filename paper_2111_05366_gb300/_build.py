@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgoat.so")
-SOURCES = ["goat_api.cu", "goat_gemm.cu", "goat_sinkhorn.cu", "goat_fw.cu", "goat_lap.cu", "goat_noalloc.cu"]
+SOURCES = ["goat_api.cu", "goat_gemm.cu", "goat_sinkhorn.cu", "goat_fw.cu", "goat_lap.cu", "goat_noalloc.cu", "goat_batched.cu", "goat_warmstart.cu"]
 HEADERS = ["goat_common.cuh", "goat_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]

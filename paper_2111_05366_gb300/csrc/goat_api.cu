@@ -21,7 +21,7 @@ namespace goat {
 enum : int { NEED_GEMM = 1, NEED_FW = 2, NEED_SK = 4, NEED_LAP = 8, NEED_HOSTCOPY = 16 };
 
 struct Plan {
-    size_t state, A16, B16, Xq, C1, GQ, P, G, f, g, deg, partial, lap, perm, Ad, Bd, Id, cost, total;
+    size_t state, A16, B16, Xq, C1, GQ, P, G, f, g, deg, partial, lap, perm, Ad, Bd, Id, cost, mlp, total;
     int ld, terms;
 };
 
@@ -52,6 +52,7 @@ static Plan make_plan(int n, int dtype, int precision, int need) {
         w.f = take((size_t)n * 4);
         w.g = take((size_t)n * 4);
         w.deg = take((size_t)2 * n * 4);
+        w.mlp = take(mlp_warm_start_scratch_bytes(n));
     }
     if (need & (NEED_SK | NEED_FW)) {
         const size_t sk = (size_t)sinkhorn_partial_elems(n) * 8;
@@ -274,8 +275,31 @@ static int match_impl(const void *A, const void *B, int n, int dtype, const floa
     int it = 0, converged = 0;
     for (; it < max_iter; ++it) {
         if (prof) cudaEventRecord(pe[0], s);
-        sinkhorn_begin(st, -1.0f, prm.sk_tol, prm.sk_warm_start ? nullptr : g, n, s);
+        const bool learned = it == 0 && prm.mlp_weights;
+        if (learned) {
+            // the learned warm start needs this step's eps on the host: eps_rel * max|G|
+            GOAT_TRY(cuda_status(cudaMemcpyAsync(pinned, &st->gmax_bits, sizeof(unsigned), cudaMemcpyDeviceToHost, s)));
+            GOAT_TRY(cuda_status(cudaStreamSynchronize(s)));
+            float gm;
+            std::memcpy(&gm, pinned, sizeof(float));
+            float e0 = eps_rel * gm;
+            if (!(e0 > 0.f)) e0 = 1.0f;
+            GOAT_TRY(mlp_warm_start_g(G, A, B, n, dtype, e0, (const __nv_bfloat16 *)prm.mlp_weights, g,
+                                      ws.at<float>(w.mlp), s));
+        }
+        sinkhorn_begin(st, -1.0f, prm.sk_tol, (prm.sk_warm_start || learned) ? nullptr : g, n, s);
         GOAT_TRY(sinkhorn_solve(G, n, n, f, g, partial, st, prm.sk_max_iter, prm.sk_check_every, pinned, s));
+        if (learned) {
+            // fallback: a learned start that does not reach the tolerance is redone cold
+            GOAT_TRY(cuda_status(cudaMemcpyAsync(pinned, &st->sk_resid, sizeof(float), cudaMemcpyDeviceToHost, s)));
+            GOAT_TRY(cuda_status(cudaStreamSynchronize(s)));
+            float r;
+            std::memcpy(&r, pinned, sizeof(float));
+            if (!(r < prm.sk_tol)) {
+                sinkhorn_begin(st, -1.0f, prm.sk_tol, g, n, s);
+                GOAT_TRY(sinkhorn_solve(G, n, n, f, g, partial, st, prm.sk_max_iter, prm.sk_check_every, pinned, s));
+            }
+        }
         if (prof) cudaEventRecord(pe[1], s);
         write_q(G, n, n, f, g, st, Xq, w.ld, w.terms, nullptr, 0, s);
         if (prof) cudaEventRecord(pe[2], s);

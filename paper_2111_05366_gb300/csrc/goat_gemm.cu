@@ -20,6 +20,7 @@
 // Two TMEM accumulators (2 x 256 columns) let the epilogue of tile t overlap
 // the MMAs of tile t+1.  Every wait is bounded (see mbar_wait_bounded).
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 
 #include "goat_common.cuh"
@@ -51,6 +52,24 @@ struct GemmParams {
     long long row_stride;   // elements between rows of the BF16 output
     int out_rows, out_cols; // rows / columns actually written
     int *err;
+    // grouped mode (many independent problems in one launch): work items
+    // {problem, tile_m, tile_n, 0} and one descriptor per problem
+    const int4 *items;
+    int num_items;
+    const GemmGroupDesc *descs;
+};
+
+// Where one output tile comes from and goes to.
+struct TileJob {
+    int x_row, y_row;       // TMA row coordinates of the X and Y tiles
+    int num_kb;             // K blocks of this tile
+    int row0, col0;         // output coordinates of the tile's first element
+    int out_rows, out_cols; // write bounds
+    int valid_cols;         // columns in [valid_cols, out_cols) are written as zero
+    float *out_f32;
+    long long ld_out;
+    __nv_bfloat16 *out_b16;
+    long long row_stride;
 };
 
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int &tm, int &tn) {
@@ -63,6 +82,43 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
     tn = r / gm;
 }
 
+template <bool GROUPED>
+__device__ __forceinline__ TileJob make_job(const GemmParams &p, int t) {
+    TileJob j;
+    if constexpr (GROUPED) {
+        const int4 it = p.items[t];
+        const GemmGroupDesc d = p.descs[it.x];
+        j.x_row = (int)(d.x_row0 + (long long)it.y * 128);
+        j.y_row = (int)(d.y_row0 + (long long)it.z * 256);
+        j.num_kb = d.num_kb;
+        j.row0 = it.y * 128;
+        j.col0 = it.z * 256;
+        j.out_rows = d.M;
+        j.out_cols = d.out_cols;
+        j.valid_cols = d.N;
+        j.out_f32 = d.out_f32;
+        j.ld_out = d.ld_out;
+        j.out_b16 = d.out_b16;
+        j.row_stride = d.row_stride;
+    } else {
+        int tm, tn;
+        tile_coords(t, p.tiles_m, p.tiles_n, tm, tn);
+        j.x_row = tm * 128;
+        j.y_row = tn * 256;
+        j.num_kb = p.num_kb;
+        j.row0 = tm * 128;
+        j.col0 = tn * 256;
+        j.out_rows = p.out_rows;
+        j.out_cols = p.out_cols;
+        j.valid_cols = 0x7fffffff;
+        j.out_f32 = p.out_f32;
+        j.ld_out = p.ld_out;
+        j.out_b16 = p.out_b16;
+        j.row_stride = p.row_stride;
+    }
+    return j;
+}
+
 __device__ __forceinline__ bool wait_timeout_ns(uint32_t bar, uint32_t parity, uint64_t ns) {
     const uint64_t t0 = global_timer_ns();
     while (!mbar_try_wait(bar, parity))
@@ -73,36 +129,41 @@ __device__ __forceinline__ bool wait_timeout_ns(uint32_t bar, uint32_t parity, u
 __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 h) { return *reinterpret_cast<uint32_t *>(&h); }
 
 // Writes one accumulator row segment (32 consecutive columns) held by this thread.
-// All indexing is static so the segment stays in registers.
-__device__ __forceinline__ void store_tile_row(const GemmParams &p, int row, int col0, const float (&v)[32]) {
-    if (row >= p.out_rows) return;
+// All indexing is static so the segment stays in registers.  Columns at or beyond
+// j.valid_cols are written as zero (padding of a grouped problem's operand).
+__device__ __forceinline__ void store_tile_row(const GemmParams &p, const TileJob &j, int row, int col0,
+                                               const float (&v)[32]) {
+    if (row >= j.out_rows || col0 >= j.out_cols) return;
     const float s = p.scale;
+    float x[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) x[c] = (col0 + c < j.valid_cols) ? v[c] * s : 0.0f;
     if (p.mode == GEMM_OUT_F32) {
-        float *dst = p.out_f32 + (long long)row * p.ld_out + col0;
-        const bool full = (col0 + 32 <= p.out_cols) && ((p.ld_out & 3) == 0);
+        float *dst = j.out_f32 + (long long)row * j.ld_out + col0;
+        const bool full = (col0 + 32 <= j.out_cols) && ((j.ld_out & 3) == 0) &&
+                          ((reinterpret_cast<uintptr_t>(dst) & 15) == 0);
         if (full) {
 #pragma unroll
             for (int c = 0; c < 32; c += 4)
-                *reinterpret_cast<float4 *>(dst + c) = make_float4(v[c] * s, v[c + 1] * s, v[c + 2] * s, v[c + 3] * s);
+                *reinterpret_cast<float4 *>(dst + c) = make_float4(x[c], x[c + 1], x[c + 2], x[c + 3]);
         } else {
 #pragma unroll
             for (int c = 0; c < 32; ++c)
-                if (col0 + c < p.out_cols) dst[c] = v[c] * s;
+                if (col0 + c < j.out_cols) dst[c] = x[c];
         }
         return;
     }
-    __nv_bfloat16 *hi = p.out_b16 + (long long)row * p.row_stride + col0;
+    __nv_bfloat16 *hi = j.out_b16 + (long long)row * j.row_stride + col0;
     __nv_bfloat16 *lo = hi + p.term_stride;
     const bool two = p.out_terms > 1;
-    const bool full = (col0 + 32 <= p.out_cols) && ((p.row_stride & 7) == 0) && ((p.term_stride & 7) == 0);
+    const bool full = (col0 + 32 <= j.out_cols) && ((j.row_stride & 7) == 0) && ((p.term_stride & 7) == 0);
     uint32_t hw[16], lw[16];
 #pragma unroll
     for (int c = 0; c < 32; c += 2) {
-        const float x0 = v[c] * s, x1 = v[c + 1] * s;
-        const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(x[c], x[c + 1]);
         const float2 hf = __bfloat1622float2(h2);
         hw[c / 2] = bf16x2_bits(h2);
-        lw[c / 2] = bf16x2_bits(__floats2bfloat162_rn(x0 - hf.x, x1 - hf.y));
+        lw[c / 2] = bf16x2_bits(__floats2bfloat162_rn(x[c] - hf.x, x[c + 1] - hf.y));
     }
     if (full) {
 #pragma unroll
@@ -117,7 +178,7 @@ __device__ __forceinline__ void store_tile_row(const GemmParams &p, int row, int
     } else {
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
-            if (col0 + c < p.out_cols) {
+            if (col0 + c < j.out_cols) {
                 const uint32_t hb = hw[c / 2], lb = lw[c / 2];
                 const unsigned short h16 = (c & 1) ? (unsigned short)(hb >> 16) : (unsigned short)(hb & 0xFFFFu);
                 const unsigned short l16 = (c & 1) ? (unsigned short)(lb >> 16) : (unsigned short)(lb & 0xFFFFu);
@@ -128,6 +189,7 @@ __device__ __forceinline__ void store_tile_row(const GemmParams &p, int row, int
     }
 }
 
+template <bool GROUPED>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm_xyT(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, const GemmParams p) {
     extern __shared__ uint8_t smem_raw[];
@@ -171,7 +233,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const int num_tiles = p.tiles_m * p.tiles_n;
+    const int num_tiles = GROUPED ? p.num_items : p.tiles_m * p.tiles_n;
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
@@ -181,9 +243,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             uint32_t issued_mask = 0, issued_parity = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-                int tm, tn;
-                tile_coords(t, p.tiles_m, p.tiles_n, tm, tn);
-                for (int kb = 0; kb < p.num_kb; ++kb) {
+                const TileJob job = make_job<GROUPED>(p, t);
+                for (int kb = 0; kb < job.num_kb; ++kb) {
                     if (!mbar_wait_bounded(empty_bar(stage), phase ^ 1u, abort_flag)) {
                         ok = false;
                         break;
@@ -191,8 +252,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                     const uint32_t sx = sbase + stage * STAGE_BYTES;
                     const int kk = kb * BK;
                     mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
-                    tma_load_2d(sx, &tmX, full_bar(stage), kk % p.kx_period, tm * BM);
-                    tma_load_2d(sx + TILE_X_BYTES, &tmY, full_bar(stage), kk, tn * BN);
+                    tma_load_2d(sx, &tmX, full_bar(stage), kk % p.kx_period, job.x_row);
+                    tma_load_2d(sx + TILE_X_BYTES, &tmY, full_bar(stage), kk, job.y_row);
                     issued_mask |= 1u << stage;
                     issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
                     if (++stage == STAGES) {
@@ -223,7 +284,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             }
             tc_fence_after();
             const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
-            for (int kb = 0; kb < p.num_kb; ++kb) {
+            const int num_kb = GROUPED ? make_job<GROUPED>(p, t).num_kb : p.num_kb;
+            for (int kb = 0; kb < num_kb; ++kb) {
                 w = (lane == 0) ? (int)mbar_wait_bounded(full_bar(stage), phase, abort_flag) : 1;
                 if (!__shfl_sync(0xffffffffu, w, 0)) {
                     ok = false;
@@ -264,12 +326,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int t = blockIdx.x; t < num_tiles; t += gridDim.x) {
-            int tm, tn;
-            tile_coords(t, p.tiles_m, p.tiles_n, tm, tn);
+            const TileJob job = make_job<GROUPED>(p, t);
             int w = (lane == 0) ? (int)mbar_wait_bounded(tfull_bar(acc), acc_phase, abort_flag) : 1;
             if (!__shfl_sync(0xffffffffu, w, 0)) break;
             tc_fence_after();
-            const int row = tm * BM + q * 32 + lane;
+            const int row = job.row0 + q * 32 + lane;
             const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1
             for (int c = 0; c < BN / 32; ++c) {
@@ -280,7 +341,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                     tc_fence_before();
                     mbar_arrive(tempty_bar(acc));
                 }
-                store_tile_row(p, row, tn * BN + c * 32, v);
+                store_tile_row(p, job, row, job.col0 + c * 32, v);
             }
             acc ^= 1;
             if (acc == 0) acc_phase ^= 1u;
@@ -334,19 +395,33 @@ static int make_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t
     return r == CUDA_SUCCESS ? GOAT_OK : GOAT_ERR_CUDA;
 }
 
-int gemm_xyT(const GemmCall &c, cudaStream_t stream) {
-    if (c.M < 1 || c.N < 1 || c.k_total < 1 || (c.k_total % BK) || (c.kx_period % BK) || c.kx_period < 1)
-        return GOAT_ERR_INVALID_ARG;
-    static int sm_count = 0;
+static int g_sm_count = 0;
+
+// One-time per process: SM count and the kernels' dynamic shared memory limit.
+static int prepare_launch() {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
         int dev = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
-        attr_err = cudaFuncSetAttribute(k_gemm_xyT, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM_BYTES);
+        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+        attr_err = cudaFuncSetAttribute(k_gemm_xyT<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)GEMM_SMEM_BYTES);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(k_gemm_xyT<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)GEMM_SMEM_BYTES);
     });
-    if (attr_err != cudaSuccess || sm_count <= 0) return GOAT_ERR_CUDA;
+    return (attr_err != cudaSuccess || g_sm_count <= 0) ? GOAT_ERR_CUDA : GOAT_OK;
+}
+
+int gemm_xyT(const GemmCall &c, cudaStream_t stream) {
+    if (c.M < 1 || c.N < 1 || c.k_total < 1 || (c.k_total % BK) || (c.kx_period % BK) || c.kx_period < 1)
+        return GOAT_ERR_INVALID_ARG;
+    {
+        const int ps = prepare_launch();
+        if (ps) return ps;
+    }
+    const int sm_count = g_sm_count;
 
     CUtensorMap mx, my;
     int st = make_map(&mx, c.X, (uint64_t)c.kx_period, (uint64_t)c.x_rows, (uint64_t)c.x_stride, BM);
@@ -374,7 +449,33 @@ int gemm_xyT(const GemmCall &c, cudaStream_t stream) {
     p.err = c.err;
     const int tiles = p.tiles_m * p.tiles_n;
     const int grid = tiles < sm_count ? tiles : sm_count;
-    k_gemm_xyT<<<grid, GEMM_THREADS, GEMM_SMEM_BYTES, stream>>>(mx, my, p);
+    k_gemm_xyT<false><<<grid, GEMM_THREADS, GEMM_SMEM_BYTES, stream>>>(mx, my, p);
+    note_launches(1);
+    return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
+}
+
+int gemm_grouped(const GemmGroupCall &c, cudaStream_t stream) {
+    if (c.num_items < 1 || c.k_extent < BK || (c.k_extent % BK)) return GOAT_ERR_INVALID_ARG;
+    int st = prepare_launch();
+    if (st) return st;
+    CUtensorMap mx, my;
+    st = make_map(&mx, c.X, (uint64_t)c.k_extent, (uint64_t)c.x_rows, (uint64_t)c.x_stride, BM);
+    if (st) return st;
+    st = make_map(&my, c.Y, (uint64_t)c.k_extent, (uint64_t)c.y_rows, (uint64_t)c.y_stride, BN);
+    if (st) return st;
+    GemmParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.kx_period = c.k_extent;
+    p.scale = c.scale;
+    p.mode = c.mode;
+    p.out_terms = 1;
+    p.term_stride = 0;
+    p.err = c.err;
+    p.items = c.items;
+    p.num_items = c.num_items;
+    p.descs = c.descs;
+    const int grid = c.num_items < g_sm_count ? c.num_items : g_sm_count;
+    k_gemm_xyT<true><<<grid, GEMM_THREADS, GEMM_SMEM_BYTES, stream>>>(mx, my, p);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
 }

@@ -39,6 +39,38 @@ struct GemmCall {
 
 int gemm_xyT(const GemmCall &c, cudaStream_t stream);
 
+// Grouped mode: many independent problems in one launch.  X and Y are stacked
+// row-wise (one 2-D tensor map each, inner extent k_extent); a problem's tiles
+// read rows from its own offsets (rows past its end belong to the next problem
+// and are masked on store).
+struct GemmGroupDesc {
+    long long x_row0, y_row0;  // first row of the problem in the stacked X / Y
+    int num_kb;                // K blocks: ceil(n / 64)
+    int M, N;                  // valid output rows / columns
+    int out_cols;              // columns written; [N, out_cols) are written as zero
+    int pad;
+    float *out_f32;
+    long long ld_out;
+    __nv_bfloat16 *out_b16;
+    long long row_stride;
+};
+
+struct GemmGroupCall {
+    const __nv_bfloat16 *X;
+    long long x_rows, x_stride;
+    const __nv_bfloat16 *Y;
+    long long y_rows, y_stride;
+    int k_extent;
+    const int4 *items;
+    int num_items;
+    const GemmGroupDesc *descs;
+    float scale;
+    int mode;
+    int *err;
+};
+
+int gemm_grouped(const GemmGroupCall &c, cudaStream_t stream);
+
 // Kernel launches issued by this host thread (every launch site reports here).
 void note_launches(int k);
 long long launches_so_far();
@@ -90,6 +122,11 @@ void sinkhorn_queue_fixed(const float *G, int n, long long ld, float *f, float *
                           int max_iter, cudaStream_t s);
 void write_q(const float *G, int n, long long ld, const float *f, const float *g, const DevState *st,
              __nv_bfloat16 *Qb, int ldq, int terms, float *Qf, long long ldf, cudaStream_t s);
+
+// goat_warmstart.cu
+size_t mlp_warm_start_scratch_bytes(int n);
+int mlp_warm_start_g(const float *G, const void *A, const void *B, int n, int dtype, float eps,
+                     const __nv_bfloat16 *w, float *g, float *scratch, cudaStream_t s);
 
 // goat_lap.cu
 int lap_chunks(int n);

@@ -400,3 +400,67 @@ def test_projection_on_gradient_variant_runs():
     gp = synthetic.rho_er_pair(50, 0.2, 1.0, seed=2)
     r = oracle.goat(gp.A, gp.B, project_on_grad=True)
     assert (r["perm"] == gp.truth).all()
+
+
+# --------------------------------------------------------------- random starts
+
+def test_splitmix64_published_first_output():
+    # SplitMix64 (Steele, Lea, Flood 2014) from state 0: the first output is 0xE220A8397B1DCDAF
+    assert oracle.splitmix64(0, 0) == 0xE220A8397B1DCDAF
+
+
+def test_random_start_is_half_barycenter_half_scaled_noise():
+    # Sec. 3.4: P0 = (J + K)/2 with K doubly stochastic, so P0 is doubly stochastic and >= 1/(2n)
+    for n, q in [(5, 0), (40, 3), (123, 17)]:
+        P0 = oracle.random_start(n, 99, q)
+        np.testing.assert_allclose(P0.sum(0), 1, atol=1e-10)
+        np.testing.assert_allclose(P0.sum(1), 1, atol=1e-10)
+        assert P0.min() >= 0.5 / n - 1e-15
+        K = 2 * P0 - 1.0 / n
+        # K is the Sinkhorn-Knopp scaling of the noise: K_ij / U_ij = u_i v_j has rank one
+        U = np.array([[((oracle.splitmix64(99, (q << 32) | (i * n + j)) >> 40) + 1) / 2 ** 24
+                       for j in range(n)] for i in range(n)])
+        R = K / U
+        np.testing.assert_allclose(R / R[:, :1] / (R[:1, :] / R[0, 0]), 1.0, rtol=1e-8)
+    assert not np.allclose(oracle.random_start(30, 1, 0), oracle.random_start(30, 1, 1))
+
+
+# --------------------------------------------------------------- learned warm start (definitions)
+
+def test_mlp_gradient_matches_central_differences():
+    rng = np.random.default_rng(0)
+    prm = rng.standard_normal(641) * 0.3
+    x = rng.standard_normal((37, 8))
+    t = rng.standard_normal(37)
+    L, grad, y = oracle.mlp_loss_grad(prm, x, t)
+    h = 1e-6
+    for k in list(range(0, 512, 53)) + [512, 530, 575, 576, 600, 639, 640]:
+        e = np.zeros(641); e[k] = h
+        Lp, _, _ = oracle.mlp_loss_grad(prm + e, x, t)
+        Lm, _, _ = oracle.mlp_loss_grad(prm - e, x, t)
+        assert grad[k] == pytest.approx((Lp - Lm) / (2 * h), rel=1e-6, abs=1e-9)
+    # outputs from the definition with numpy
+    W1, b1, w2, b2 = prm[:512].reshape(64, 8), prm[512:576], prm[576:640], prm[640]
+    np.testing.assert_allclose(y, np.tanh(x @ W1.T + b1) @ w2 + b2, rtol=1e-12)
+    assert L == pytest.approx(np.mean((y - t) ** 2), rel=1e-12)
+
+
+def test_dual_features_closed_form_at_barycenter():
+    # at the barycenter G = -(2/n) d_A d_B^T: row i is -(2/n) d_A(i) d_B, column j is -(2/n) d_B(j) d_A
+    gp = synthetic.rho_er_pair(60, 0.2, 0.8, seed=3)
+    A, B = gp.A.astype(float), gp.B.astype(float)
+    n = 60
+    dA, dB = A.sum(1), B.sum(1)
+    G = -2.0 / n * np.outer(dA, dB)
+    eps = 0.03 * np.abs(G).max()
+    F = oracle.dual_features(G, A, B, eps)
+    c = -2.0 / n / eps
+    np.testing.assert_allclose(F[:n, 2], c * dA * dB.mean(), rtol=1e-12)
+    np.testing.assert_allclose(F[:n, 3], c * dA * dB.min(), rtol=1e-12)
+    np.testing.assert_allclose(F[:n, 5], c * dA * dB.max(), rtol=1e-12)
+    np.testing.assert_allclose(F[:n, 4], -c * dA * dB.std(), rtol=1e-9)
+    np.testing.assert_allclose(F[n:, 2], c * dB * dA.mean(), rtol=1e-12)
+    np.testing.assert_allclose(F[:n, 0], dA / dA.mean(), rtol=1e-12)
+    np.testing.assert_allclose(F[n:, 1], (B @ dB) / (B @ dB).mean(), rtol=1e-12)
+    assert (F[:n, 6] == 0).all() and (F[n:, 6] == 1).all()
+    np.testing.assert_allclose(F[:, 7], np.log(n) / 10)
