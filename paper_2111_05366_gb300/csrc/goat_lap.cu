@@ -29,6 +29,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <cooperative_groups.h>
+
 #include "goat_common.cuh"
 #include "goat_internal.h"
 
@@ -253,6 +255,169 @@ __global__ void __launch_bounds__(1024) k_lap_tail(const float *__restrict__ M, 
     if (tid == 0) st->lap_unassigned = s_tail - s_head;
 }
 
+// The same Gauss-Seidel tail spread over a cluster of 8 CTAs: CTA r owns the
+// columns [r W, (r + 1) W) and keeps their prices and owners in its shared
+// memory; for each bid every CTA scans its part of the bidder's row, the leader
+// (rank 0) merges the 8 partial top-2s it receives through distributed shared
+// memory, updates the winning column's price and owner in the owner CTA, the
+// queue and assign[], and broadcasts the next bidder.  Two cluster barriers per
+// bid; each CTA prefetches its part of the next queued row into L2 while it
+// scans the current one.
+constexpr int LAP_CLUSTER = 8;
+
+__global__ void __cluster_dims__(LAP_CLUSTER, 1, 1) __launch_bounds__(256)
+    k_lap_tail_cluster(const float *__restrict__ M, int n, const Quant q, const LapBuffers L, i64 eps,
+                       long long max_bids, DevState *st) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int W = (n + LAP_CLUSTER - 1) / LAP_CLUSTER;
+    const int c0 = min(n, rank * W), c1 = min(n, c0 + W);
+    extern __shared__ unsigned char lap_sm[];
+    i64 *price_s = reinterpret_cast<i64 *>(lap_sm);
+    int *owner_s = reinterpret_cast<int *>(price_s + W);
+    __shared__ i64 s_wb1[8], s_wb2[8];
+    __shared__ int s_wj1[8];
+    __shared__ i64 s_b1[LAP_CLUSTER], s_b2[LAP_CLUSTER];  // leader: partial results of the cluster
+    __shared__ int s_j1[LAP_CLUSTER];
+    __shared__ int s_next;                                // next bidder (-1: stop), set by the leader
+    __shared__ int s_pref;                                // the bidder after it, if already queued (-1: none)
+    __shared__ int s_head, s_tail;
+    __shared__ long long s_bids;
+
+    for (int j = c0 + tid; j < c1; j += blockDim.x) {
+        price_s[j - c0] = L.price[j];
+        owner_s[j - c0] = L.owner[j];
+    }
+    cluster.sync();  // every CTA of the cluster is running before any shared memory of another is touched
+    if (rank == 0) {
+        if (tid == 0) {
+            s_head = 0;
+            s_tail = 0;
+            s_bids = 0;
+        }
+        __syncthreads();
+        for (int base = 0; base < n; base += blockDim.x) {  // queue the unassigned rows in row order
+            const int i = base + tid;
+            const bool fr = i < n && L.assign[i] < 0;
+            const unsigned m = __ballot_sync(0xffffffffu, fr);
+            __shared__ int s_cnt[8];
+            if (lane == 0) s_cnt[warp] = __popc(m);
+            __syncthreads();
+            int off = s_tail;
+            for (int w = 0; w < warp; ++w) off += s_cnt[w];
+            if (fr) L.queue[off + __popc(m & ((1u << lane) - 1u))] = i;
+            __syncthreads();
+            if (tid == 0) {
+                int add = 0;
+                for (int w = 0; w < nwarps; ++w) add += s_cnt[w];
+                s_tail += add;
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            const bool more = s_head != s_tail && max_bids > 0;
+            const int nx = more ? L.queue[s_head % n] : -1;
+            const int np = (more && s_tail - s_head > 1) ? L.queue[(s_head + 1) % n] : -1;
+            for (int r = 0; r < LAP_CLUSTER; ++r) {
+                *cluster.map_shared_rank(&s_next, r) = nx;
+                *cluster.map_shared_rank(&s_pref, r) = np;
+            }
+        }
+    }
+    cluster.sync();
+    while (true) {
+        const int i = s_next;
+        if (i < 0) break;  // uniform over the cluster: the leader wrote the same value everywhere
+        const int pf = s_pref;
+        if (pf >= 0) {  // the likely next bidder: pull this CTA's part of its row into L2
+            const float *row = M + (long long)pf * n;
+            for (int j = c0 + tid * 32; j < c1; j += blockDim.x * 32)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(row + j));
+        }
+        i64 b1 = kNegInf, b2 = kNegInf;
+        int j1 = INT_MAX;
+        const float *Mi = M + (long long)i * n;
+        int j = c0 + tid;
+        for (; j + 3 * (int)blockDim.x < c1; j += 4 * blockDim.x) {  // four loads in flight per thread
+            float v4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v4[u] = __ldg(Mi + j + u * blockDim.x);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int jj = j + u * blockDim.x;
+                const i64 v = benefit(v4[u], q) - price_s[jj - c0];
+                if (v > b1) {
+                    b2 = b1;
+                    b1 = v;
+                    j1 = jj;
+                } else if (v > b2) {
+                    b2 = v;
+                }
+            }
+        }
+        for (; j < c1; j += blockDim.x) {
+            const i64 v = benefit(__ldg(Mi + j), q) - price_s[j - c0];
+            if (v > b1) {
+                b2 = b1;
+                b1 = v;
+                j1 = j;
+            } else if (v > b2) {
+                b2 = v;
+            }
+        }
+        top2_warp(b1, b2, j1);
+        if (lane == 0) {
+            s_wb1[warp] = b1;
+            s_wb2[warp] = b2;
+            s_wj1[warp] = j1;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < nwarps; ++w) top2_merge(b1, b2, j1, s_wb1[w], s_wb2[w], s_wj1[w]);
+            *cluster.map_shared_rank(&s_b1[rank], 0) = b1;
+            *cluster.map_shared_rank(&s_b2[rank], 0) = b2;
+            *cluster.map_shared_rank(&s_j1[rank], 0) = j1;
+        }
+        cluster.sync();
+        if (rank == 0 && tid == 0) {
+            b1 = s_b1[0];
+            b2 = s_b2[0];
+            j1 = s_j1[0];
+            for (int r = 1; r < LAP_CLUSTER; ++r) top2_merge(b1, b2, j1, s_b1[r], s_b2[r], s_j1[r]);
+            const i64 inc = (b2 == kNegInf) ? eps : (b1 - b2) + eps;
+            const int ro = j1 / W, jl = j1 - ro * W;
+            i64 *pp = cluster.map_shared_rank(price_s, ro);
+            int *po = cluster.map_shared_rank(owner_s, ro);
+            pp[jl] += inc;
+            const int old = po[jl];
+            po[jl] = i;
+            L.assign[i] = j1;
+            ++s_head;
+            if (old >= 0) {
+                L.assign[old] = -1;
+                L.queue[s_tail % n] = old;
+                ++s_tail;
+            }
+            ++s_bids;
+            const bool more = s_head != s_tail && s_bids < max_bids;
+            const int nx = more ? L.queue[s_head % n] : -1;
+            const int np = (more && s_tail - s_head > 1) ? L.queue[(s_head + 1) % n] : -1;
+            for (int r = 0; r < LAP_CLUSTER; ++r) {
+                *cluster.map_shared_rank(&s_next, r) = nx;
+                *cluster.map_shared_rank(&s_pref, r) = np;
+            }
+        }
+        cluster.sync();
+    }
+    for (int j = c0 + tid; j < c1; j += blockDim.x) {
+        L.price[j] = price_s[j - c0];
+        L.owner[j] = owner_s[j - c0];
+    }
+    if (rank == 0 && tid == 0) st->lap_unassigned = s_tail - s_head;
+}
+
 // Completes a partial assignment: each unassigned row (in row order) takes the
 // free object of largest a_ij - p_j.  One CTA; used only when the last phase ran
 // out of its bid budget.
@@ -394,6 +559,16 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
     int rounds = 0;
     bool exhausted = false;
     const int head_threshold = std::max(32, n / 256);
+    // the cluster tail for large n (its columns' prices and owners must fit a CTA's shared memory)
+    const int cw = (n + LAP_CLUSTER - 1) / LAP_CLUSTER;
+    const size_t cluster_smem = (size_t)cw * (sizeof(i64) + sizeof(int));
+    bool use_cluster = n >= 4096 && cluster_smem <= 160 * 1024;
+    if (use_cluster &&
+        cudaFuncSetAttribute(k_lap_tail_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        use_cluster = false;
+    }
     for (;;) {
         const bool last = eps <= 1;
         k_lap_reset<<<g1, 256, 0, s>>>(n, L, st, 0);
@@ -414,7 +589,11 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
         }
         if (left > 0) {
             const long long budget = last ? std::max(4LL * n, 262144LL) : std::max((long long)n, 65536LL);
-            k_lap_tail<<<1, 1024, 0, s>>>(M, n, q, L, eps, budget, st);
+            if (use_cluster) {
+                k_lap_tail_cluster<<<LAP_CLUSTER, 256, cluster_smem, s>>>(M, n, q, L, eps, budget, st);
+            } else {
+                k_lap_tail<<<1, 1024, 0, s>>>(M, n, q, L, eps, budget, st);
+            }
             note_launches(1);
             left = poll_int(&st->lap_unassigned, host_pinned, s);
         }

@@ -238,6 +238,24 @@ def test_project_real_matrices(n):
             assert abs(cost - cost_o) <= tol, (kind, mx, cost, cost_o)
 
 
+@pytest.mark.parametrize("n,kind,mx", [(4100, "uniform", True), (4100, "uniform", False), (4100, "relaxed", True),
+                                       (6007, "uniform", False)])
+def test_project_large_matrices(n, kind, mx):
+    # sizes that take the clustered Gauss-Seidel tail (columns split over 8 CTAs,
+    # the last CTA's share ragged) against the oracle's Hungarian optimum
+    rng = np.random.default_rng(n + int(mx))
+    if kind == "uniform":
+        M = rng.random((n, n)).astype(np.float32)
+    else:
+        M = random_ds(n, n).astype(np.float32) + 1e-3 * rng.random((n, n)).astype(np.float32)
+    perm, cost, gap = goat.goat_project(cuda(M), maximize=mx)
+    p = perm.cpu().numpy()
+    assert sorted(p) == list(range(n))
+    _, cost_o = oracle.lap(M, maximize=mx)
+    assert abs(cost - cost_o) <= n * 2.0 ** -52 * float(np.abs(M).max()) * 4, (cost, cost_o)
+    assert oracle.assignment_cost_f32(M, p) == cost
+
+
 # ------------------------------------------------------------------ objective
 
 def test_objective_exact():
