@@ -279,9 +279,9 @@ def run_kernel_case(args):
         del G
         e0.record()
         for _ in range(args.repeat):
-            _, cost, gap = goat.goat_project(Q, allow_uncertified=True)
+            _, cost, gap, info = goat.goat_project_ex(Q, allow_uncertified=True)
         e1.record()
-        out["cost"], out["gap"] = cost, gap
+        out["cost"], out["gap"], out["info"] = cost, gap, info
     torch.cuda.synchronize()
     out["ms_per_call"] = e0.elapsed_time(e1) / args.repeat
     print(json.dumps(out), flush=True)
@@ -446,7 +446,8 @@ def main():
         for _ in range(warmup):
             _, _, stw = solve(params)
             log(f"warmup solve: {stw['fw_iters']} FW iters, {stw['ms_total']:.0f} ms "
-                f"(fw {stw['ms_fw']:.0f}, project {stw['ms_project']:.0f}, lap rounds {stw['lap_rounds']})")
+                f"(fw {stw['ms_fw']:.0f}, project {stw['ms_project']:.0f}, lap rounds {stw['lap_rounds']}, "
+                f"tail bids {stw['lap_tail_bids']}, sap rows {stw['lap_sap_rows']} pops {stw['lap_sap_pops']})")
         barrier()
         torch.cuda.synchronize()
         if sampler:
@@ -496,7 +497,8 @@ def main():
                  "projection_share": ms_proj / ms, "sinkhorn_iters_per_fw_iter": sk_total / max(fw_iters, 1),
                  "fw_iters_per_solve": fw_iters / args.steps, "accuracy": acc,
                  "objective": st["objective"], "disagreements": st["disagreements"], "lap_gap": st["lap_gap"],
-                 "lap_rounds": st["lap_rounds"]}
+                 "lap_rounds": st["lap_rounds"], "lap_tail_bids": st["lap_tail_bids"],
+                 "lap_sap_rows": st["lap_sap_rows"], "lap_sap_pops": st["lap_sap_pops"]}
     if sk_total:
         # one Sinkhorn iteration reads G twice (row pass + column pass): 8 n^2 bytes
         breakdown["sinkhorn_gbs_two_pass"] = 8.0 * n * n / (ms_sk / sk_total / 1000.0) / 1e9

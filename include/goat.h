@@ -119,6 +119,9 @@ typedef struct goat_stats {
     float ms_sinkhorn;                 /* Sinkhorn solves, host polls included              */
     float ms_step;                     /* Q materialisation, line search and update          */
     long long launches;                /* kernels launched by the call                       */
+    long long lap_tail_bids;           /* projection: sequential auction bids                */
+    int lap_sap_rows;                  /* projection: rows placed by augmenting-path searches */
+    long long lap_sap_pops;            /* projection: row scans of those searches            */
 } goat_stats;
 
 /* Fills *p with the defaults listed above. */
@@ -205,14 +208,55 @@ GOAT_API int goat_fw_update(float *P, float *G, const float *Q, const float *G_Q
 /*
  * goat_project -- the final linear assignment (Alg. 3 return line):
  * perm = argmax (maximize = 1) or argmin (0) of sum_i M[i][perm i] over permutations.
- * GPU auction with eps-scaling, then an exact price-relaxation pass that
- * either certifies the assignment optimal (LP duality) or repairs it.
+ * Exact: the entries are quantised to 64-bit integers (40 bits below the largest
+ * |M|, scaled by a power of two Qm > n), solved by an eps-scaling auction whose
+ * stragglers are placed by shortest augmenting paths, and certified optimal for
+ * the quantised matrix by LP duality (gap < 1 quantum).
  *   M         device n x n float.     perm_out  device int32[n].
  *   cost_out  HOST double: sum_i M[i][perm i] in FP64, row order (nullable).
- *   gap_out   HOST double: dual minus primal after certification (nullable).
+ *   gap_out   HOST double: dual minus primal, in units of M (0 when certified) (nullable).
+ * Returns GOAT_ERR_NOT_CONVERGED (perm still a valid permutation) when the budgets
+ * ran out before the certificate; GOAT_ERR_NAN for a non-finite entry.
  */
 GOAT_API int goat_project(const float *M, int n, int maximize, int32_t *perm_out, double *cost_out, double *gap_out,
                  void *workspace, size_t workspace_bytes, goat_stream_t stream);
+
+/* Schedule of the projection's auction (negative fields: built-in default). */
+typedef struct goat_lap_options {
+    int max_rounds;       /* parallel (Jacobi) bidding rounds over all phases, default 1<<20   */
+    int head_rounds;      /* Jacobi rounds per eps phase before the sequential steps (the rounds
+                             stop early once at most 16 rows bid), default 256                */
+    long long tail_bids;  /* sequential (Gauss-Seidel) bids per phase, default max(n, 65536),
+                             max(4n, 262144) in the last phase; 0 skips that step            */
+    long long tail_stall; /* bids in a row that do not shorten the queue of unassigned rows
+                             and end the sequential bidding, default max(512, n / 32)         */
+    long long sap_pops;   /* row scans the shortest-augmenting-path searches may do per phase,
+                             default 8n + 2^16 (64n + 2^20 in the last phase); 0 disables them */
+} goat_lap_options;
+
+/* What one projection did. */
+typedef struct goat_lap_info {
+    int phases;           /* eps phases                                          */
+    int rounds;           /* Jacobi rounds                                       */
+    long long tail_bids;  /* Gauss-Seidel bids                                   */
+    int sap_rows;         /* rows placed by augmenting-path searches             */
+    long long sap_pops;   /* rows those searches scanned (a row again after its label fell) */
+    long long sap_steps;  /* grid-wide parallel steps of those searches          */
+    int filled;           /* rows filled greedily after every budget ran out     */
+    double ms_head, ms_tail, ms_sap; /* host wall time of each kind of step, polls included */
+} goat_lap_info;
+
+/* Fills *o with the defaults (all fields -1 except max_rounds and head_rounds). */
+GOAT_API void goat_lap_default_options(goat_lap_options *o);
+
+/*
+ * goat_project_ex -- goat_project with an explicit schedule (opts, nullable:
+ * defaults) and a report of the work done (info, HOST, nullable).  The result is
+ * the same optimum whatever the schedule; only the time and the budgets change.
+ */
+GOAT_API int goat_project_ex(const float *M, int n, int maximize, const goat_lap_options *opts, int32_t *perm_out,
+                    double *cost_out, double *gap_out, goat_lap_info *info, void *workspace, size_t workspace_bytes,
+                    goat_stream_t stream);
 
 /*
  * goat_objective -- f(perm) = sum_ij A_ij B[perm i][perm j] (eq. QAP at a permutation)

@@ -40,7 +40,7 @@ EXPORTED = ["goat_default_params", "goat_strerror", "goat_workspace_bytes", "goa
             "goat_gradient", "goat_sinkhorn", "goat_line_search", "goat_fw_update", "goat_project",
             "goat_objective", "goat_gemm_bf16_xyT", "goat_sinkhorn_noalloc", "goat_match_batched",
             "goat_workspace_bytes_batched", "goat_dual_features", "goat_mlp_forward", "goat_mlp_train_step",
-            "goat_mlp_warm_start"]
+            "goat_mlp_warm_start", "goat_lap_default_options", "goat_project_ex"]
 
 
 class GoatError(RuntimeError):
@@ -63,7 +63,21 @@ class goat_stats(ctypes.Structure):
                 ("disagreements", ctypes.c_double), ("lap_gap", ctypes.c_double), ("lap_rounds", ctypes.c_int),
                 ("ms_total", ctypes.c_float), ("ms_fw", ctypes.c_float), ("ms_project", ctypes.c_float),
                 ("ms_gemm", ctypes.c_float), ("gemm_launches", ctypes.c_int), ("ms_sinkhorn", ctypes.c_float),
-                ("ms_step", ctypes.c_float), ("launches", ctypes.c_longlong)]
+                ("ms_step", ctypes.c_float), ("launches", ctypes.c_longlong),
+                ("lap_tail_bids", ctypes.c_longlong), ("lap_sap_rows", ctypes.c_int),
+                ("lap_sap_pops", ctypes.c_longlong)]
+
+
+class goat_lap_options(ctypes.Structure):
+    _fields_ = [("max_rounds", ctypes.c_int), ("head_rounds", ctypes.c_int), ("tail_bids", ctypes.c_longlong),
+                ("tail_stall", ctypes.c_longlong), ("sap_pops", ctypes.c_longlong)]
+
+
+class goat_lap_info(ctypes.Structure):
+    _fields_ = [("phases", ctypes.c_int), ("rounds", ctypes.c_int), ("tail_bids", ctypes.c_longlong),
+                ("sap_rows", ctypes.c_int), ("sap_pops", ctypes.c_longlong), ("sap_steps", ctypes.c_longlong),
+                ("filled", ctypes.c_int),
+                ("ms_head", ctypes.c_double), ("ms_tail", ctypes.c_double), ("ms_sap", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -101,6 +115,9 @@ def load():
             "goat_fw_update": (_i, [_vp, _vp, _vp, _vp, _i, _d, _vp]),
             "goat_project": (_i, [_vp, _i, _i, _vp, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp, ctypes.c_size_t,
                                   _vp]),
+            "goat_lap_default_options": (None, [ctypes.POINTER(goat_lap_options)]),
+            "goat_project_ex": (_i, [_vp, _i, _i, ctypes.POINTER(goat_lap_options), _vp, ctypes.POINTER(_d),
+                                     ctypes.POINTER(_d), ctypes.POINTER(goat_lap_info), _vp, ctypes.c_size_t, _vp]),
             "goat_objective": (_i, [_vp, _vp, _i, _i, _vp, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp,
                                     ctypes.c_size_t, _vp]),
             "goat_gemm_bf16_xyT": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _i, _f, _vp, _i, _i, _i, _vp]),
@@ -192,7 +209,8 @@ def _stats_dict(st: goat_stats) -> dict:
             "objective": st.objective, "disagreements": st.disagreements, "lap_gap": st.lap_gap,
             "lap_rounds": st.lap_rounds, "ms_total": st.ms_total, "ms_fw": st.ms_fw, "ms_project": st.ms_project,
             "ms_gemm": st.ms_gemm, "gemm_launches": st.gemm_launches, "ms_sinkhorn": st.ms_sinkhorn,
-            "ms_step": st.ms_step, "launches": st.launches}
+            "ms_step": st.ms_step, "launches": st.launches, "lap_tail_bids": st.lap_tail_bids,
+            "lap_sap_rows": st.lap_sap_rows, "lap_sap_pops": st.lap_sap_pops}
 
 
 # ---------------------------------------------------------------- entry points
@@ -317,6 +335,31 @@ def goat_project(M, maximize: bool = True, allow_uncertified: bool = False):
     allow = (GOAT_OK, GOAT_ERR_NOT_CONVERGED) if allow_uncertified else (GOAT_OK,)
     _check(r, "goat_project", allow)
     return perm, cost.value, gap.value
+
+
+def lap_options(**overrides) -> goat_lap_options:
+    """The projection's default schedule with `overrides` applied (see goat_lap_options)."""
+    o = goat_lap_options()
+    load().goat_lap_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def goat_project_ex(M, maximize: bool = True, options=None, allow_uncertified: bool = False):
+    """goat_project with an explicit schedule; returns (perm, cost, gap, info dict)."""
+    torch = _torch()
+    n = M.shape[0]
+    perm = torch.empty(n, dtype=torch.int32, device=M.device)
+    cost, gap = ctypes.c_double(), ctypes.c_double()
+    info = goat_lap_info()
+    opt = ctypes.byref(options) if options is not None else None
+    r = load().goat_project_ex(_dev(M, torch.float32, (n, n), "M"), n, int(bool(maximize)), opt,
+                               _dev(perm, torch.int32, (n,), "perm"), ctypes.byref(cost), ctypes.byref(gap),
+                               ctypes.byref(info), None, 0, _stream())
+    allow = (GOAT_OK, GOAT_ERR_NOT_CONVERGED) if allow_uncertified else (GOAT_OK,)
+    _check(r, "goat_project_ex", allow)
+    return perm, cost.value, gap.value, {f: getattr(info, f) for f, _ in goat_lap_info._fields_}
 
 
 def goat_objective(A, B, perm):

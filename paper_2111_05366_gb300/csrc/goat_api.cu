@@ -335,15 +335,18 @@ static int match_impl(const void *A, const void *B, int n, int dtype, const floa
 
     // projection onto the permutations
     double gap = 0.0;
-    int rounds = 0;
+    LapControl ctl;
+    lap_default_control(&ctl);
+    ctl.max_rounds = prm.lap_max_rounds;
+    LapReport rep{};
     int lst;
     if (prm.project_on_grad) {
         // argmax tr(Pi^T grad f(P)) = argmin <Pi, G>
-        lst = lap_solve(G, n, 0, perm_dev, ws.at<void>(w.lap), st, prm.lap_max_rounds, ws.at<double>(w.cost) + 6,
-                        pinned, &gap, &rounds, s);
+        lst = lap_solve(G, n, 0, perm_dev, ws.at<void>(w.lap), st, ctl, ws.at<double>(w.cost) + 6, pinned, &gap,
+                        &rep, s);
     } else {
-        lst = lap_solve(P, n, 1, perm_dev, ws.at<void>(w.lap), st, prm.lap_max_rounds, ws.at<double>(w.cost) + 6,
-                        pinned, &gap, &rounds, s);
+        lst = lap_solve(P, n, 1, perm_dev, ws.at<void>(w.lap), st, ctl, ws.at<double>(w.cost) + 6, pinned, &gap,
+                        &rep, s);
     }
     if (lst != GOAT_OK && lst != GOAT_ERR_NOT_CONVERGED) return lst;
     cudaEventRecord(ev[3], s);
@@ -385,7 +388,10 @@ static int match_impl(const void *A, const void *B, int n, int dtype, const floa
         stats->objective = fobj;
         stats->disagreements = dis;
         stats->lap_gap = gap;
-        stats->lap_rounds = rounds;
+        stats->lap_rounds = rep.rounds;
+        stats->lap_tail_bids = rep.tail_bids;
+        stats->lap_sap_rows = rep.sap_rows;
+        stats->lap_sap_pops = rep.sap_pops;
         cudaEventElapsedTime(&stats->ms_total, ev[0], ev[3]);
         cudaEventElapsedTime(&stats->ms_fw, ev[1], ev[2]);
         cudaEventElapsedTime(&stats->ms_project, ev[2], ev[3]);
@@ -578,24 +584,43 @@ int goat_fw_update(float *P, float *G, const float *Q, const float *G_Q, int n, 
     return cuda_status(cudaGetLastError());
 }
 
-int goat_project(const float *M, int n, int maximize, int32_t *perm_out, double *cost_out, double *gap_out,
-                 void *workspace, size_t workspace_bytes, goat_stream_t stream) {
+void goat_lap_default_options(goat_lap_options *o) {
+    if (!o) return;
+    LapControl c;
+    lap_default_control(&c);
+    o->max_rounds = c.max_rounds;
+    o->head_rounds = c.head_rounds;
+    o->tail_bids = c.tail_bids;
+    o->tail_stall = c.tail_stall;
+    o->sap_pops = c.sap_pops;
+}
+
+int goat_project_ex(const float *M, int n, int maximize, const goat_lap_options *opts, int32_t *perm_out,
+                    double *cost_out, double *gap_out, goat_lap_info *info, void *workspace, size_t workspace_bytes,
+                    goat_stream_t stream) {
     if (!M || !perm_out || n < 1) return GOAT_ERR_INVALID_ARG;
     GOAT_TRY(device_ok());
     int *pinned = pinned_words();
     if (!pinned) return GOAT_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
+    LapControl ctl;
+    lap_default_control(&ctl);
+    if (opts) {
+        if (opts->max_rounds > 0) ctl.max_rounds = opts->max_rounds;
+        if (opts->head_rounds >= 0) ctl.head_rounds = opts->head_rounds;
+        ctl.tail_bids = opts->tail_bids;
+        ctl.tail_stall = opts->tail_stall;
+        ctl.sap_pops = opts->sap_pops;
+    }
     const Plan w = make_plan(n, GOAT_DTYPE_U8, GOAT_PREC_BF16, NEED_LAP);
     Scratch ws;
     GOAT_TRY(ws.acquire(workspace, workspace_bytes, w.total, s));
     DevState *st = ws.at<DevState>(w.state);
     GOAT_TRY(init_state(st, 0.03f, maximize ? 1 : 0, 0.0f, s));
     double gap = 0.0;
-    int rounds = 0;
-    goat_params d;
-    goat_default_params(&d);
-    const int r = lap_solve(M, n, maximize ? 1 : 0, perm_out, ws.at<void>(w.lap), st, d.lap_max_rounds,
-                            ws.at<double>(w.cost) + 6, pinned, &gap, &rounds, s);
+    LapReport rep{};
+    const int r = lap_solve(M, n, maximize ? 1 : 0, perm_out, ws.at<void>(w.lap), st, ctl, ws.at<double>(w.cost) + 6,
+                            pinned, &gap, &rep, s);
     if (r != GOAT_OK && r != GOAT_ERR_NOT_CONVERGED) return r;
     double cost = 0.0;
     GOAT_TRY(cuda_status(
@@ -603,7 +628,25 @@ int goat_project(const float *M, int n, int maximize, int32_t *perm_out, double 
     GOAT_TRY(cuda_status(cudaStreamSynchronize(s)));
     if (cost_out) *cost_out = cost;
     if (gap_out) *gap_out = gap;
+    if (info) {
+        info->phases = rep.phases;
+        info->rounds = rep.rounds;
+        info->tail_bids = rep.tail_bids;
+        info->sap_rows = rep.sap_rows;
+        info->sap_pops = rep.sap_pops;
+        info->sap_steps = rep.sap_epochs;
+        info->filled = rep.filled;
+        info->ms_head = rep.ms_head;
+        info->ms_tail = rep.ms_tail;
+        info->ms_sap = rep.ms_sap;
+    }
     return r;
+}
+
+int goat_project(const float *M, int n, int maximize, int32_t *perm_out, double *cost_out, double *gap_out,
+                 void *workspace, size_t workspace_bytes, goat_stream_t stream) {
+    return goat_project_ex(M, n, maximize, nullptr, perm_out, cost_out, gap_out, nullptr, workspace, workspace_bytes,
+                           stream);
 }
 
 int goat_objective(const void *A, const void *B, int n, int dtype_AB, const int32_t *perm, double *objective_out,

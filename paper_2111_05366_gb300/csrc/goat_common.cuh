@@ -40,11 +40,14 @@ struct DevState {
     int lap_unassigned;   // auction: bidders without an object
     int lap_changed;      // price relaxation: any price raised this round
     int lap_phase_done;
-    int pad0;
+    int lap_free;         // shortest-augmenting-path step: rows it has to place
     int asym_count;
     int bad_perm;
     double lap_eps;
     double lap_gap;
+    long long lap_bids;   // Gauss-Seidel bids of the projection so far
+    long long lap_pops;   // rows scanned by its shortest-augmenting-path searches
+    long long lap_epochs; // grid-wide steps of those searches
     // traces (indexed by fw_iter)
     int tr_sk_iters[GOAT_TRACE_MAX];
     float tr_sk_resid[GOAT_TRACE_MAX];

@@ -131,7 +131,22 @@ int mlp_warm_start_g(const float *G, const void *A, const void *B, int n, int dt
 // goat_lap.cu
 int lap_chunks(int n);
 size_t lap_bytes(int n, int nchunks);
-int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_ws, DevState *st, int max_rounds,
-              double *cost_dev, int *host_pinned, double *gap_host, int *rounds_host, cudaStream_t s);
+// Controls of the projection's schedule (negative: the built-in default).
+struct LapControl {
+    int max_rounds;        // Jacobi rounds over all phases
+    int head_rounds;       // Jacobi rounds per phase before the sequential steps
+    long long tail_bids;   // Gauss-Seidel bids per phase
+    long long tail_stall;  // bids without the queue shrinking that end the Gauss-Seidel tail
+    long long sap_pops;    // row scans the augmenting-path searches may do per phase (0: none)
+};
+void lap_default_control(LapControl *c);
+struct LapReport {
+    int phases, rounds, sap_rows, filled;
+    long long tail_bids, sap_pops, sap_epochs;
+    double ms_head, ms_tail, ms_sap;
+};
+int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_ws, DevState *st,
+              const LapControl &ctl, double *cost_dev, int *host_pinned, double *gap_host, LapReport *rep,
+              cudaStream_t s);
 
 }  // namespace goat

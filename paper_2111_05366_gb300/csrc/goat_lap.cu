@@ -19,12 +19,24 @@
 // an exact LAP, no tolerance involved.
 //
 // Scheduling.  Parallel Jacobi rounds while many rows bid; the long tail of a
-// phase (a few rows evicting each other) runs in one persistent CTA in
-// Gauss-Seidel order.  Budgets bound the time on degenerate (near-tied) inputs:
-// a phase that runs out ends early (the next restarts from the prices reached);
-// if the last phase runs out, the free rows are filled greedily and the returned
-// duality gap says how far from optimal that is (0 when the proof above applies).
+// phase (a few rows evicting each other) runs in Gauss-Seidel order in one CTA,
+// or for n >= 4096 in a cluster of 8 CTAs that split the columns.  When that tail
+// stops shrinking (a few rows chasing the last free objects through a large set
+// of near-tied objects: each bid lifts one price by about eps, so closing a gap
+// of D costs about |set| D / eps bids), the remaining rows are placed by
+// shortest augmenting paths instead (Jonker-Volgenant's Dijkstra step, one
+// search per row, exact integer duals).  The search runs on the matrix a~ that
+// adds to each assigned pair its eps-complementary-slackness slack
+// delta_i = max_j (a_ij - p_j) - (a_i,j_i - p_j_i) in [0, eps], so that the
+// auction's prices and assignment are an exactly feasible, tight starting point.
+// Every assignment value of a~ is within n eps of that of a; in the last phase
+// (eps = 1 < Qm / n) an optimum of a~ is therefore an optimum of a.  A phase thus
+// always ends complete, and its prices are a sound start for the next one.
+// Budgets bound the time on degenerate inputs: if the last phase still runs out,
+// the free rows are filled greedily and the returned duality gap says how far
+// from optimal that is (0 when the proof above applies).
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -38,14 +50,27 @@ namespace goat {
 
 typedef long long i64;
 
+// Grid-wide reduction slot of the augmenting-path searches (one per barrier epoch).
+struct SapSlot {
+    long long minv;  // least label of the open columns
+    long long tmin;  // least label of the free columns in the bucket
+    int count;       // rows appended to the epoch's frontier list
+    int tj;          // lowest free bucket column with label tmin
+};
+
 struct LapBuffers {
     i64 *price, *my_bid;
     int *owner, *assign, *my_obj, *bwin, *queue;
     unsigned long long *bbest;
+    int *sap_pred;    // predecessor row of every column after a search
+    int *frow[2];     // frontier lists (rows to scan) of alternate epochs
+    i64 *fh[2];       // their label offsets
+    SapSlot *ring;    // 4 reduction slots
 };
 
 size_t lap_bytes(int n, int /*nchunks*/) {
-    return 2 * (size_t)n * sizeof(i64) + 5 * (size_t)n * sizeof(int) + (size_t)n * 8 + 16 * 256;
+    return 2 * (size_t)n * sizeof(i64) + 5 * (size_t)n * sizeof(int) + (size_t)n * 8 + 16 * 256 +
+           (size_t)n * sizeof(int) + 2 * (size_t)n * (sizeof(int) + sizeof(i64)) + 4 * sizeof(SapSlot) + 6 * 256;
 }
 
 static LapBuffers carve(void *base, int n) {
@@ -64,6 +89,12 @@ static LapBuffers carve(void *base, int n) {
     L.bwin = (int *)take(sizeof(int) * n);
     L.queue = (int *)take(sizeof(int) * n);
     L.bbest = (unsigned long long *)take(sizeof(unsigned long long) * n);
+    L.sap_pred = (int *)take(sizeof(int) * n);
+    L.frow[0] = (int *)take(sizeof(int) * n);
+    L.frow[1] = (int *)take(sizeof(int) * n);
+    L.fh[0] = (i64 *)take(sizeof(i64) * n);
+    L.fh[1] = (i64 *)take(sizeof(i64) * n);
+    L.ring = (SapSlot *)take(4 * sizeof(SapSlot));
     return L;
 }
 
@@ -145,29 +176,38 @@ __global__ void k_lap_reset(int n, const LapBuffers L, DevState *st, int reset_p
     if (blockIdx.x == 0 && threadIdx.x == 0) st->lap_unassigned = n;
 }
 
-// Jacobi bidding: one warp per unassigned row.
+// Jacobi bidding: one CTA per unassigned row (a row of 4n bytes is too long for
+// one warp to stream at speed once few rows are left bidding).
 __global__ void __launch_bounds__(256) k_lap_bid(const float *__restrict__ M, int n, const Quant q,
                                                  const LapBuffers L, i64 eps, const DevState *st) {
     if (st->lap_unassigned == 0) return;
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int i = gw; i < n; i += nw) {
-        if (L.assign[i] >= 0) {
-            if (lane == 0) L.my_obj[i] = -1;
+    __shared__ i64 s_b1[8], s_b2[8];
+    __shared__ int s_j1[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        if (L.assign[i] >= 0) {  // block-uniform: assign[] does not change during the kernel
+            if (tid == 0) L.my_obj[i] = -1;
             continue;
         }
         i64 b1 = kNegInf, b2 = kNegInf;
         int j1 = INT_MAX;
-        top2_scan(M + (long long)i * n, L.price, n, q, lane, 32, b1, b2, j1);
+        top2_scan(M + (long long)i * n, L.price, n, q, tid, blockDim.x, b1, b2, j1);
         top2_warp(b1, b2, j1);
         if (lane == 0) {
+            s_b1[warp] = b1;
+            s_b2[warp] = b2;
+            s_j1[warp] = j1;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < nwarps; ++w) top2_merge(b1, b2, j1, s_b1[w], s_b2[w], s_j1[w]);
             const i64 inc = (b2 == kNegInf) ? eps : (b1 - b2) + eps;
             const i64 bid = L.price[j1] + inc;
             L.my_obj[i] = j1;
             L.my_bid[i] = bid;
             atomicMax(&L.bbest[j1], (unsigned long long)bid);  // bids are non-negative
         }
+        __syncthreads();
     }
 }
 
@@ -200,9 +240,11 @@ __global__ void k_lap_assign(int n, const LapBuffers L, DevState *st) {
 // Gauss-Seidel tail of a phase: one CTA serves the unassigned rows one at a
 // time; a bid takes its object at once and the evicted holder joins the queue
 // (a ring of n slots: a row is queued only while unassigned).  All threads scan
-// the bidder's row.  At most max_bids bids.
+// the bidder's row.  At most max_bids bids; stops early once `stall` bids in a
+// row have not shortened the queue below its shortest length so far.
 __global__ void __launch_bounds__(1024) k_lap_tail(const float *__restrict__ M, int n, const Quant q,
-                                                   const LapBuffers L, i64 eps, long long max_bids, DevState *st) {
+                                                   const LapBuffers L, i64 eps, long long max_bids, long long stall,
+                                                   DevState *st) {
     __shared__ i64 s_b1[32], s_b2[32];
     __shared__ int s_j1[32];
     __shared__ int s_head, s_tail, s_stop;
@@ -216,7 +258,8 @@ __global__ void __launch_bounds__(1024) k_lap_tail(const float *__restrict__ M, 
     for (int i = tid; i < n; i += blockDim.x)
         if (L.assign[i] < 0) L.queue[atomicAdd(&s_tail, 1)] = i;
     __syncthreads();
-    long long bids = 0;
+    long long bids = 0, since = 0;
+    int qmin = s_tail - s_head;
     while (true) {
         if (s_head == s_tail || s_stop) break;
         const int i = L.queue[s_head % n];
@@ -247,12 +290,22 @@ __global__ void __launch_bounds__(1024) k_lap_tail(const float *__restrict__ M, 
                     L.queue[s_tail % n] = old;
                     ++s_tail;
                 }
-                if (++bids > max_bids) s_stop = 1;
+                const int len = s_tail - s_head;
+                if (len < qmin) {
+                    qmin = len;
+                    since = 0;
+                } else {
+                    ++since;
+                }
+                if (++bids >= max_bids || since >= stall) s_stop = 1;
             }
         }
         __syncthreads();
     }
-    if (tid == 0) st->lap_unassigned = s_tail - s_head;
+    if (tid == 0) {
+        st->lap_unassigned = s_tail - s_head;
+        st->lap_bids += bids;
+    }
 }
 
 // The same Gauss-Seidel tail spread over a cluster of 8 CTAs: CTA r owns the
@@ -267,7 +320,7 @@ constexpr int LAP_CLUSTER = 8;
 
 __global__ void __cluster_dims__(LAP_CLUSTER, 1, 1) __launch_bounds__(256)
     k_lap_tail_cluster(const float *__restrict__ M, int n, const Quant q, const LapBuffers L, i64 eps,
-                       long long max_bids, DevState *st) {
+                       long long max_bids, long long stall, DevState *st) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -284,7 +337,8 @@ __global__ void __cluster_dims__(LAP_CLUSTER, 1, 1) __launch_bounds__(256)
     __shared__ int s_next;                                // next bidder (-1: stop), set by the leader
     __shared__ int s_pref;                                // the bidder after it, if already queued (-1: none)
     __shared__ int s_head, s_tail;
-    __shared__ long long s_bids;
+    __shared__ long long s_bids, s_since;
+    __shared__ int s_qmin;
 
     for (int j = c0 + tid; j < c1; j += blockDim.x) {
         price_s[j - c0] = L.price[j];
@@ -317,7 +371,9 @@ __global__ void __cluster_dims__(LAP_CLUSTER, 1, 1) __launch_bounds__(256)
             __syncthreads();
         }
         if (tid == 0) {
-            const bool more = s_head != s_tail && max_bids > 0;
+            s_qmin = s_tail - s_head;
+            s_since = 0;
+            const bool more = s_head != s_tail && max_bids > 0 && stall > 0;
             const int nx = more ? L.queue[s_head % n] : -1;
             const int np = (more && s_tail - s_head > 1) ? L.queue[(s_head + 1) % n] : -1;
             for (int r = 0; r < LAP_CLUSTER; ++r) {
@@ -401,7 +457,14 @@ __global__ void __cluster_dims__(LAP_CLUSTER, 1, 1) __launch_bounds__(256)
                 ++s_tail;
             }
             ++s_bids;
-            const bool more = s_head != s_tail && s_bids < max_bids;
+            const int len = s_tail - s_head;
+            if (len < s_qmin) {
+                s_qmin = len;
+                s_since = 0;
+            } else {
+                ++s_since;
+            }
+            const bool more = s_head != s_tail && s_bids < max_bids && s_since < stall;
             const int nx = more ? L.queue[s_head % n] : -1;
             const int np = (more && s_tail - s_head > 1) ? L.queue[(s_head + 1) % n] : -1;
             for (int r = 0; r < LAP_CLUSTER; ++r) {
@@ -415,7 +478,344 @@ __global__ void __cluster_dims__(LAP_CLUSTER, 1, 1) __launch_bounds__(256)
         L.price[j] = price_s[j - c0];
         L.owner[j] = owner_s[j - c0];
     }
-    if (rank == 0 && tid == 0) st->lap_unassigned = s_tail - s_head;
+    if (rank == 0 && tid == 0) {
+        st->lap_unassigned = s_tail - s_head;
+        st->lap_bids += s_bids;
+    }
+}
+
+// ---------------------------------------------------------------- shortest augmenting paths
+
+// Slack of every assigned row, delta_i = max_j (a_ij - p_j) - (a_i,j_i - p_j_i) >= 0,
+// into my_bid[i], and its object into my_obj[i] (the pairs whose benefit a~ adds
+// delta_i); the unassigned rows are listed in queue[0, lap_free).  One warp per row.
+__global__ void __launch_bounds__(256) k_lap_sap_prep(const float *__restrict__ M, int n, const Quant q,
+                                                      const LapBuffers L, DevState *st) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = gw; i < n; i += nw) {
+        const int ji = L.assign[i];
+        if (ji < 0) {
+            if (lane == 0) {
+                L.my_obj[i] = -1;
+                L.my_bid[i] = 0;
+                L.queue[atomicAdd(&st->lap_free, 1)] = i;
+            }
+            continue;
+        }
+        const float *Mi = M + (long long)i * n;
+        i64 b1 = kNegInf, b2 = kNegInf;
+        int j1 = INT_MAX;
+        top2_scan(Mi, L.price, n, q, lane, 32, b1, b2, j1);
+        top2_warp(b1, b2, j1);
+        if (lane == 0) {
+            const i64 d = b1 - (benefit(Mi[ji], q) - L.price[ji]);
+            L.my_obj[i] = ji;
+            L.my_bid[i] = d > 0 ? d : 0;
+        }
+    }
+}
+
+constexpr int SAP_THREADS = 256;
+constexpr i64 kPosInf = LLONG_MAX / 4;
+
+// Reduced cost of (i, j) in the minimisation form: c~_ij = -a~_ij, the benefit of
+// the pair (i, j0_i) raised by the row's slack delta_i.
+__device__ __forceinline__ i64 sap_cost(float m, const Quant q, int j, int j0, i64 delta) {
+    return -(benefit(m, q) + (j == j0 ? delta : 0));
+}
+
+// Block-wide minimum of (x, j) pairs, lowest j on ties; the result is valid in thread 0.
+__device__ __forceinline__ void block_argmin(i64 &x, int &j, i64 *sx, int *sj) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const i64 ox = __shfl_xor_sync(0xffffffffu, x, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, j, o);
+        if (ox < x || (ox == x && oj < j)) {
+            x = ox;
+            j = oj;
+        }
+    }
+    if (lane == 0) {
+        sx[warp] = x;
+        sj[warp] = j;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (sx[w] < x || (sx[w] == x && sj[w] < j)) {
+                x = sx[w];
+                j = sj[w];
+            }
+    __syncthreads();
+}
+
+// Shortest augmenting paths for the rows listed in queue[0, lap_free), on the whole
+// GPU (a cooperative launch; every thread owns CPT columns, j = global thread +
+// c * total threads, and keeps their dual v_j = -p_j, label d_j, predecessor row,
+// owner and state -- open, in the current bucket, or closed -- in registers).
+// One search per row, Dijkstra by label buckets: all open columns with a label
+// <= mu + Delta (mu the least open label) join the bucket; the rows owning them are
+// scanned in parallel (each thread relaxes its columns over the listed rows), and
+// bucket columns whose label drops are scanned again, until the bucket is stable
+// (label-correcting, so the labels are exact whatever Delta).  A free column in a
+// stable bucket ends the search with the least such label (lowest index on ties):
+// the scanned columns' duals move by d_j - d_t and the leader flips the path.  The
+// sequence of results is that of Jonker-Volgenant's sequential Dijkstra; Delta
+// (starting at delta0, widened while buckets stay small) only sets how many rows go
+// into one parallel step.  Control flow depends only on values read after a grid
+// barrier, so every block takes the same path.  At most max_scans row scans per
+// launch; rows left over stay unassigned (lap_unassigned reports them).
+template <int CPT>
+__global__ void __launch_bounds__(SAP_THREADS) k_lap_sap_grid(const float *__restrict__ M, int n, const Quant q,
+                                                              const LapBuffers L, i64 delta0, long long max_scans,
+                                                              DevState *st) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int gthreads = gridDim.x * blockDim.x;
+    const int gt = blockIdx.x * blockDim.x + tid;
+    const bool leader = blockIdx.x == 0 && tid == 0;
+    __shared__ i64 s_x[SAP_THREADS / 32];
+    __shared__ int s_j[SAP_THREADS / 32];
+
+    int col[CPT], pred[CPT], own[CPT];
+    i64 v[CPT], d[CPT];
+    unsigned char stt[CPT];  // 0 open, 1 in the bucket, 2 closed
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+        col[c] = gt + c * gthreads;
+        const bool ok = col[c] < n;
+        v[c] = ok ? -L.price[col[c]] : 0;
+        own[c] = ok ? L.owner[col[c]] : -1;
+        d[c] = kPosInf;
+        pred[c] = -1;
+        stt[c] = 2;
+    }
+    // Reduction slots: the one of epoch e (e = barriers passed) is written during e,
+    // read during e + 1 and reset by the leader during e + 2 (ring of 4).
+    int e = 0;
+    if (leader)
+        for (int k = 0; k < 4; ++k) {
+            L.ring[k].minv = kPosInf;
+            L.ring[k].tmin = kPosInf;
+            L.ring[k].count = 0;
+            L.ring[k].tj = INT_MAX;
+        }
+    auto barrier = [&]() {
+        grid.sync();
+        ++e;
+        if (leader) {
+            SapSlot &z = L.ring[(e + 2) & 3];
+            z.minv = kPosInf;
+            z.tmin = kPosInf;
+            z.count = 0;
+            z.tj = INT_MAX;
+        }
+    };
+    auto cur = [&]() -> SapSlot & { return L.ring[e & 3]; };
+    auto prev = [&]() -> const SapSlot & { return L.ring[(e + 3) & 3]; };
+    // appends (row, h) to this epoch's frontier list, one atomic per warp and column slot
+    auto append = [&](int c, bool want, int row, i64 h) {
+        const unsigned m = __ballot_sync(0xffffffffu, want);
+        if (!m) return;
+        int base = 0;
+        const int first = __ffs(m) - 1;
+        if (lane == first) base = atomicAdd(&cur().count, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, first);
+        if (want) {
+            const int k = base + __popc(m & ((1u << lane) - 1u));
+            L.frow[e & 1][k] = row;
+            L.fh[e & 1][k] = h;
+        }
+        (void)c;
+    };
+    // label offset h_i = d_j - (c~_ij - v_j) of the row owning column j
+    auto row_offset = [&](int c) -> i64 {
+        const int i = own[c];
+        return d[c] - (sap_cost(M[(long long)i * n + col[c]], q, col[c], L.my_obj[i], L.my_bid[i]) - v[c]);
+    };
+    barrier();
+
+    const int nfree = *(volatile int *)&st->lap_free;
+    long long scans = 0;
+    int solved = 0;
+    bool aborted = false;
+    for (int k = 0; k < nfree && !aborted; ++k) {
+        const int i0 = L.queue[k];
+        {
+            const float *Mi = M + (long long)i0 * n;
+            i64 lmin = kPosInf;
+            int lj = INT_MAX;
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                if (col[c] < n) {
+                    d[c] = sap_cost(__ldg(Mi + col[c]), q, col[c], -1, 0) - v[c];
+                    pred[c] = i0;
+                    stt[c] = 0;
+                    if (d[c] < lmin) lmin = d[c];
+                }
+            }
+            block_argmin(lmin, lj, s_x, s_j);
+            if (tid == 0) atomicMin(&cur().minv, lmin);
+        }
+        barrier();
+        i64 mu = prev().minv;
+        i64 Delta = delta0 > 0 ? delta0 : 1;
+        int t = -1;
+        i64 dt = 0;
+        while (true) {  // buckets
+            if (mu >= kPosInf) {  // no open column left: cannot happen while a row is free
+                aborted = true;
+                break;
+            }
+            const i64 tau = mu > kPosInf - Delta ? kPosInf : mu + Delta;
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const bool in = col[c] < n && stt[c] == 0 && d[c] <= tau;
+                if (in) stt[c] = 1;
+                const bool want = in && own[c] >= 0;
+                append(c, want, want ? own[c] : 0, want ? row_offset(c) : 0);
+            }
+            barrier();
+            int cnt = prev().count;
+            long long bucket_scans = 0;
+            while (cnt > 0) {  // relaxations until the bucket is stable
+                scans += cnt;
+                bucket_scans += cnt;
+                if (scans > max_scans) {
+                    aborted = true;
+                    break;
+                }
+                const int *fr = L.frow[(e + 1) & 1];
+                const i64 *fh = L.fh[(e + 1) & 1];
+                bool ch[CPT];
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) ch[c] = false;
+                constexpr int RU = CPT >= 8 ? 2 : 16 / CPT;  // rows in flight: 16 loads per thread
+                for (int r0 = 0; r0 < cnt; r0 += RU) {
+                    int rows[RU];
+                    float m[RU][CPT];
+#pragma unroll
+                    for (int u = 0; u < RU; ++u) {
+                        rows[u] = r0 + u < cnt ? fr[r0 + u] : -1;
+#pragma unroll
+                        for (int c = 0; c < CPT; ++c)
+                            m[u][c] = (rows[u] >= 0 && col[c] < n) ? __ldg(M + (long long)rows[u] * n + col[c]) : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < RU; ++u) {
+                        if (rows[u] < 0) break;
+                        const i64 h = fh[r0 + u];
+                        const int j0 = L.my_obj[rows[u]];
+                        const i64 dl = L.my_bid[rows[u]];
+#pragma unroll
+                        for (int c = 0; c < CPT; ++c) {
+                            if (col[c] < n && stt[c] != 2) {
+                                const i64 nd = h + sap_cost(m[u][c], q, col[c], j0, dl) - v[c];
+                                if (nd < d[c]) {
+                                    d[c] = nd;
+                                    pred[c] = rows[u];
+                                    ch[c] = true;
+                                }
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) {
+                    if (ch[c] && stt[c] == 0 && d[c] <= tau) stt[c] = 1;
+                    const bool want = ch[c] && stt[c] == 1 && own[c] >= 0;
+                    append(c, want, want ? own[c] : 0, want ? row_offset(c) : 0);
+                }
+                barrier();
+                cnt = prev().count;
+            }
+            if (aborted) break;
+            // the bucket is stable: its free columns end the search, else it closes
+            i64 lt = kPosInf, lm = kPosInf;
+            int dummy = INT_MAX;
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                if (col[c] >= n) continue;
+                if (stt[c] == 1 && own[c] < 0 && d[c] < lt) lt = d[c];
+                if (stt[c] == 0 && d[c] < lm) lm = d[c];
+            }
+            block_argmin(lt, dummy, s_x, s_j);
+            if (tid == 0) atomicMin(&cur().tmin, lt);
+            dummy = INT_MAX;
+            block_argmin(lm, dummy, s_x, s_j);
+            if (tid == 0) atomicMin(&cur().minv, lm);
+            barrier();
+            const i64 tm = prev().tmin;
+            if (tm < kPosInf) {
+                int lj = INT_MAX;
+                i64 z = 0;
+#pragma unroll
+                for (int c = 0; c < CPT; ++c)
+                    if (col[c] < n && stt[c] == 1 && own[c] < 0 && d[c] == tm && col[c] < lj) lj = col[c];
+                block_argmin(z, lj, s_x, s_j);
+                if (tid == 0) atomicMin(&cur().tj, lj);
+                barrier();
+                t = prev().tj;
+                dt = tm;
+                break;
+            }
+            mu = prev().minv;
+#pragma unroll
+            for (int c = 0; c < CPT; ++c)
+                if (stt[c] == 1) stt[c] = 2;
+            if (bucket_scans < 32) {
+                Delta = Delta > (kPosInf >> 3) ? kPosInf : Delta * 4;
+            } else if (bucket_scans > 8192 && Delta / 2 >= (delta0 > 0 ? delta0 : 1)) {
+                Delta /= 2;
+            }
+        }
+        if (aborted || t < 0 || t >= n) {
+            aborted = true;
+            break;
+        }
+        // duals of the settled columns; predecessors for the path walk
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+            if (col[c] < n) {
+                if (stt[c] != 0 && d[c] < dt) v[c] += d[c] - dt;
+                L.sap_pred[col[c]] = pred[c];
+            }
+        barrier();
+        if (leader) {
+            int j = t;
+            for (int hop = 0; hop <= n; ++hop) {
+                const int i = L.sap_pred[j];
+                if (i < 0 || i >= n) {
+                    st->error = GOAT_ERR_NOT_CONVERGED;
+                    break;
+                }
+                L.owner[j] = i;
+                const int jn = L.assign[i];
+                L.assign[i] = j;
+                if (i == i0 || jn < 0) break;
+                j = jn;
+            }
+        }
+        barrier();
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+            if (col[c] < n) own[c] = L.owner[col[c]];
+        ++solved;
+    }
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+        if (col[c] < n) {
+            L.price[col[c]] = -v[c];
+            L.owner[col[c]] = own[c];
+        }
+    if (leader) {
+        st->lap_unassigned = nfree - solved;
+        st->lap_pops += scans;
+        st->lap_epochs += e;
+    }
 }
 
 // Completes a partial assignment: each unassigned row (in row order) takes the
@@ -522,16 +922,29 @@ static int poll_int(const int *dev, int *pinned, cudaStream_t s) {
     return *pinned;
 }
 
+void lap_default_control(LapControl *c) {
+    c->max_rounds = 1 << 20;
+    c->head_rounds = 256;
+    c->tail_bids = -1;
+    c->tail_stall = -1;
+    c->sap_pops = -1;
+}
+
 // Runs the projection.  lap_ws must hold lap_bytes(n, ...) bytes; cost_dev
 // points at >= 2 doubles (the assignment cost, then the gap accumulator).
-int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_ws, DevState *st, int max_rounds,
-              double *cost_dev, int *host_pinned, double *gap_host, int *rounds_host, cudaStream_t s) {
+int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_ws, DevState *st,
+              const LapControl &ctl, double *cost_dev, int *host_pinned, double *gap_host, LapReport *rep,
+              cudaStream_t s) {
+    using clk = std::chrono::steady_clock;
+    auto ms_since = [](clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); };
+    LapReport R{};
     LapBuffers L = carve(lap_ws, n);
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), sms * 8));
     const int gbid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 8), sms * 16));
+    const int growb = (int)std::max<int64_t>(1, std::min<int64_t>(n, sms * 8));  // one CTA per bidding row
 
     // scale: max |M| < C' = 2^e
     unsigned *cbits = reinterpret_cast<unsigned *>(&st->gmax_next);
@@ -555,51 +968,101 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
 
     k_lap_reset<<<g1, 256, 0, s>>>(n, L, st, 1);
     note_launches(1);
+    cudaMemsetAsync(&st->lap_bids, 0, 3 * sizeof(long long), s);
     i64 eps = std::max<i64>(1, c_int / 4);
     int rounds = 0;
     bool exhausted = false;
-    const int head_threshold = std::max(32, n / 256);
-    // the cluster tail for large n (its columns' prices and owners must fit a CTA's shared memory)
+    const int head_threshold = 16;
+    // the cluster kernels hold per-column state of n / 8 columns in each CTA's shared memory
     const int cw = (n + LAP_CLUSTER - 1) / LAP_CLUSTER;
-    const size_t cluster_smem = (size_t)cw * (sizeof(i64) + sizeof(int));
-    bool use_cluster = n >= 4096 && cluster_smem <= 160 * 1024;
-    if (use_cluster &&
-        cudaFuncSetAttribute(k_lap_tail_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem) !=
+    const size_t tail_smem = (size_t)cw * (sizeof(i64) + sizeof(int));
+    bool use_cluster_tail = n >= 4096 && tail_smem <= 160 * 1024;
+    if (use_cluster_tail &&
+        cudaFuncSetAttribute(k_lap_tail_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tail_smem) !=
             cudaSuccess) {
         cudaGetLastError();
-        use_cluster = false;
+        use_cluster_tail = false;
     }
+    // the augmenting-path searches: a cooperative grid with CPT columns per thread
+    int sap_cpt = 0, sap_grid = 0;
+    if (ctl.sap_pops != 0) {
+        for (int c : {1, 2, 4, 8}) {
+            if ((long long)sms * SAP_THREADS * c >= n) {
+                sap_cpt = c;
+                break;
+            }
+        }
+        int coop = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        if (!coop) sap_cpt = 0;
+        if (sap_cpt) sap_grid = (int)std::max<int64_t>(1, ceil_div(n, (int64_t)SAP_THREADS * sap_cpt));
+    }
+    const bool use_sap = sap_cpt > 0;
+    const long long stall = ctl.tail_stall >= 0 ? ctl.tail_stall : std::max(512LL, (long long)n / 32);
     for (;;) {
         const bool last = eps <= 1;
+        ++R.phases;
         k_lap_reset<<<g1, 256, 0, s>>>(n, L, st, 0);
         note_launches(1);
         int left = n;
-        for (int hr = 0; hr < 64 && rounds < max_rounds; hr += 2) {
-            for (int b = 0; b < 2; ++b) {
-                k_lap_bid<<<gbid, 256, 0, s>>>(M, n, q, L, eps, st);
+        auto t0 = clk::now();
+        for (int hr = 0; hr < ctl.head_rounds && rounds < ctl.max_rounds; hr += 4) {
+            for (int b = 0; b < 4; ++b) {
+                k_lap_bid<<<growb, 256, 0, s>>>(M, n, q, L, eps, st);
                 note_launches(1);
                 k_lap_win<<<g1, 256, 0, s>>>(n, L, st);
                 note_launches(1);
                 k_lap_assign<<<g1, 256, 0, s>>>(n, L, st);
                 note_launches(1);
             }
-            rounds += 2;
+            rounds += 4;
             left = poll_int(&st->lap_unassigned, host_pinned, s);
             if (left <= head_threshold) break;
         }
-        if (left > 0) {
-            const long long budget = last ? std::max(4LL * n, 262144LL) : std::max((long long)n, 65536LL);
-            if (use_cluster) {
-                k_lap_tail_cluster<<<LAP_CLUSTER, 256, cluster_smem, s>>>(M, n, q, L, eps, budget, st);
+        R.ms_head += ms_since(t0);
+        const long long budget = ctl.tail_bids >= 0 ? ctl.tail_bids
+                                 : last             ? std::max(4LL * n, 262144LL)
+                                                    : std::max((long long)n, 65536LL);
+        if (left > 0 && budget > 0) {
+            t0 = clk::now();
+            if (use_cluster_tail) {
+                k_lap_tail_cluster<<<LAP_CLUSTER, 256, tail_smem, s>>>(M, n, q, L, eps, budget, stall, st);
             } else {
-                k_lap_tail<<<1, 1024, 0, s>>>(M, n, q, L, eps, budget, st);
+                k_lap_tail<<<1, 1024, 0, s>>>(M, n, q, L, eps, budget, stall, st);
             }
             note_launches(1);
             left = poll_int(&st->lap_unassigned, host_pinned, s);
+            R.ms_tail += ms_since(t0);
+        }
+        if (left > 0 && use_sap) {
+            t0 = clk::now();
+            const long long pops =
+                ctl.sap_pops > 0 ? ctl.sap_pops : (last ? 64LL * n + (1LL << 20) : 8LL * n + (1LL << 16));
+            cudaMemsetAsync(&st->lap_free, 0, sizeof(int), s);
+            k_lap_sap_prep<<<gbid, 256, 0, s>>>(M, n, q, L, st);
+            i64 delta0 = std::max<i64>(1, eps);
+            long long max_scans = pops;
+            DevState *stp = st;
+            const float *Mp = M;
+            int nn = n;
+            void *args[] = {(void *)&Mp, (void *)&nn, (void *)&q, (void *)&L, (void *)&delta0, (void *)&max_scans,
+                            (void *)&stp};
+            const void *fn = sap_cpt == 1   ? (const void *)k_lap_sap_grid<1>
+                             : sap_cpt == 2 ? (const void *)k_lap_sap_grid<2>
+                             : sap_cpt == 4 ? (const void *)k_lap_sap_grid<4>
+                                            : (const void *)k_lap_sap_grid<8>;
+            if (cudaLaunchCooperativeKernel(fn, dim3(sap_grid), dim3(SAP_THREADS), args, 0, s) != cudaSuccess)
+                return GOAT_ERR_CUDA;
+            note_launches(2);
+            R.sap_rows += left;
+            left = poll_int(&st->lap_unassigned, host_pinned, s);
+            R.sap_rows -= left;
+            R.ms_sap += ms_since(t0);
         }
         if (last) {
             if (left > 0) {
                 exhausted = true;
+                R.filled = left;
                 k_lap_fill<<<1, 1024, 0, s>>>(M, n, q, L, st);
                 note_launches(1);
             }
@@ -618,12 +1081,18 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
     k_lap_gap<<<gbid, 256, 0, s>>>(M, n, q, L, gap_dev);
     note_launches(1);
     double gq = 0.0;
+    long long counts[3] = {0, 0, 0};
     cudaMemcpyAsync(&gq, gap_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(counts, &st->lap_bids, sizeof(counts), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return GOAT_ERR_CUDA;
     const bool optimal = !exhausted && gq < (double)q.qm;
     const double unit = std::ldexp(1.0, e - bq) / (double)q.qm;  // one quantised unit in units of M
     if (gap_host) *gap_host = optimal ? 0.0 : gq * unit;
-    if (rounds_host) *rounds_host = rounds;
+    R.rounds = rounds;
+    R.tail_bids = counts[0];
+    R.sap_pops = counts[1];
+    R.sap_epochs = counts[2];
+    if (rep) *rep = R;
     return optimal ? GOAT_OK : GOAT_ERR_NOT_CONVERGED;
 }
 

@@ -256,6 +256,55 @@ def test_project_large_matrices(n, kind, mx):
     assert oracle.assignment_cost_f32(M, p) == cost
 
 
+@pytest.mark.parametrize("n", [1, 2, 9, 64, 250])
+def test_project_augmenting_paths_only_integer_bitwise(n):
+    # no bidding at all: every row of every eps phase is placed by the shortest
+    # augmenting path searches; integer matrices with many ties
+    rng = np.random.default_rng(100 + n)
+    M = rng.integers(0, 20, size=(n, n)).astype(np.float32)
+    opts = goat.lap_options(head_rounds=0, tail_bids=0, sap_pops=4 * n * n + 64)
+    for mx in (True, False):
+        perm, cost, gap, info = goat.goat_project_ex(cuda(M), maximize=mx, options=opts)
+        p = perm.cpu().numpy()
+        assert sorted(p) == list(range(n))
+        assert cost == oracle.lap(M.astype(np.float64), maximize=mx)[1]
+        assert gap == 0.0 and info["filled"] == 0 and info["tail_bids"] == 0
+        assert info["sap_rows"] == n * info["phases"]
+
+
+@pytest.mark.parametrize("n", [100, 513])
+def test_project_augmenting_paths_finish_real_matrices(n):
+    # a short parallel head, no sequential bidding: the stragglers of each phase
+    # go to the augmenting-path searches; the optimum must equal the oracle's
+    for seed, kind in enumerate(["uniform", "relaxed"]):
+        rng = np.random.default_rng(7 * n + seed)
+        if kind == "uniform":
+            M = rng.random((n, n)).astype(np.float32)
+        else:
+            M = random_ds(n, seed).astype(np.float32) + 1e-3 * rng.random((n, n)).astype(np.float32)
+        opts = goat.lap_options(head_rounds=2, tail_bids=0)
+        perm, cost, gap, info = goat.goat_project_ex(cuda(M), maximize=True, options=opts)
+        _, cost_o = oracle.lap(M, maximize=True)
+        assert abs(cost - cost_o) <= n * 2.0 ** -52 * float(np.abs(M).max()) * 4, (kind, cost, cost_o)
+        assert gap == 0.0 and info["sap_rows"] > 0 and info["filled"] == 0
+        # the default schedule reaches the same optimum
+        _, cost_d, _, _ = goat.goat_project_ex(cuda(M), maximize=True)
+        assert cost_d == cost
+
+
+def test_project_sap_budget_exhaustion_still_returns_a_permutation():
+    # a search budget of one column per phase cannot finish: the rows are filled
+    # greedily and the call reports an uncertified result with a positive gap
+    n = 300
+    M = np.random.default_rng(3).random((n, n)).astype(np.float32)
+    opts = goat.lap_options(head_rounds=0, tail_bids=0, sap_pops=1)
+    perm, cost, gap, info = goat.goat_project_ex(cuda(M), maximize=True, options=opts, allow_uncertified=True)
+    p = perm.cpu().numpy()
+    assert sorted(p) == list(range(n))
+    assert info["filled"] > 0 and gap > 0.0
+    assert oracle.assignment_cost_f32(M, p) == cost
+
+
 # ------------------------------------------------------------------ objective
 
 def test_objective_exact():
