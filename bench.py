@@ -447,7 +447,8 @@ def main():
             _, _, stw = solve(params)
             log(f"warmup solve: {stw['fw_iters']} FW iters, {stw['ms_total']:.0f} ms "
                 f"(fw {stw['ms_fw']:.0f}, project {stw['ms_project']:.0f}, lap rounds {stw['lap_rounds']}, "
-                f"tail bids {stw['lap_tail_bids']}, sap rows {stw['lap_sap_rows']} pops {stw['lap_sap_pops']})")
+                f"tail bids {stw['lap_tail_bids']}, sap rows {stw['lap_sap_rows']} pops {stw['lap_sap_pops']}; "
+                f"ms head {stw['lap_ms_head']:.0f} tail {stw['lap_ms_tail']:.0f} sap {stw['lap_ms_sap']:.0f})")
         barrier()
         torch.cuda.synchronize()
         if sampler:
@@ -498,7 +499,8 @@ def main():
                  "fw_iters_per_solve": fw_iters / args.steps, "accuracy": acc,
                  "objective": st["objective"], "disagreements": st["disagreements"], "lap_gap": st["lap_gap"],
                  "lap_rounds": st["lap_rounds"], "lap_tail_bids": st["lap_tail_bids"],
-                 "lap_sap_rows": st["lap_sap_rows"], "lap_sap_pops": st["lap_sap_pops"]}
+                 "lap_sap_rows": st["lap_sap_rows"], "lap_sap_pops": st["lap_sap_pops"],
+                 "lap_ms_head": st["lap_ms_head"], "lap_ms_tail": st["lap_ms_tail"], "lap_ms_sap": st["lap_ms_sap"]}
     if sk_total:
         # one Sinkhorn iteration reads G twice (row pass + column pass): 8 n^2 bytes
         breakdown["sinkhorn_gbs_two_pass"] = 8.0 * n * n / (ms_sk / sk_total / 1000.0) / 1e9

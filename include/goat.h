@@ -122,6 +122,8 @@ typedef struct goat_stats {
     long long lap_tail_bids;           /* projection: sequential auction bids                */
     int lap_sap_rows;                  /* projection: rows placed by augmenting-path searches */
     long long lap_sap_pops;            /* projection: row scans of those searches            */
+    float lap_ms_head, lap_ms_tail, lap_ms_sap; /* projection: host wall time of its bidding rounds,
+                                          sequential bids and augmenting-path searches         */
 } goat_stats;
 
 /* Fills *p with the defaults listed above. */

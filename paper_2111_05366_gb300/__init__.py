@@ -65,7 +65,8 @@ class goat_stats(ctypes.Structure):
                 ("ms_gemm", ctypes.c_float), ("gemm_launches", ctypes.c_int), ("ms_sinkhorn", ctypes.c_float),
                 ("ms_step", ctypes.c_float), ("launches", ctypes.c_longlong),
                 ("lap_tail_bids", ctypes.c_longlong), ("lap_sap_rows", ctypes.c_int),
-                ("lap_sap_pops", ctypes.c_longlong)]
+                ("lap_sap_pops", ctypes.c_longlong), ("lap_ms_head", ctypes.c_float),
+                ("lap_ms_tail", ctypes.c_float), ("lap_ms_sap", ctypes.c_float)]
 
 
 class goat_lap_options(ctypes.Structure):
@@ -210,7 +211,8 @@ def _stats_dict(st: goat_stats) -> dict:
             "lap_rounds": st.lap_rounds, "ms_total": st.ms_total, "ms_fw": st.ms_fw, "ms_project": st.ms_project,
             "ms_gemm": st.ms_gemm, "gemm_launches": st.gemm_launches, "ms_sinkhorn": st.ms_sinkhorn,
             "ms_step": st.ms_step, "launches": st.launches, "lap_tail_bids": st.lap_tail_bids,
-            "lap_sap_rows": st.lap_sap_rows, "lap_sap_pops": st.lap_sap_pops}
+            "lap_sap_rows": st.lap_sap_rows, "lap_sap_pops": st.lap_sap_pops, "lap_ms_head": st.lap_ms_head,
+            "lap_ms_tail": st.lap_ms_tail, "lap_ms_sap": st.lap_ms_sap}
 
 
 # ---------------------------------------------------------------- entry points

@@ -392,6 +392,9 @@ static int match_impl(const void *A, const void *B, int n, int dtype, const floa
         stats->lap_tail_bids = rep.tail_bids;
         stats->lap_sap_rows = rep.sap_rows;
         stats->lap_sap_pops = rep.sap_pops;
+        stats->lap_ms_head = (float)rep.ms_head;
+        stats->lap_ms_tail = (float)rep.ms_tail;
+        stats->lap_ms_sap = (float)rep.ms_sap;
         cudaEventElapsedTime(&stats->ms_total, ev[0], ev[3]);
         cudaEventElapsedTime(&stats->ms_fw, ev[1], ev[2]);
         cudaEventElapsedTime(&stats->ms_project, ev[2], ev[3]);

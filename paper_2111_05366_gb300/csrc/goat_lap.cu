@@ -56,6 +56,7 @@ struct SapSlot {
     long long tmin;  // least label of the free columns in the bucket
     int count;       // rows appended to the epoch's frontier list
     int tj;          // lowest free bucket column with label tmin
+    int hist[64];    // open non-free columns by bit length of (label - base)
 };
 
 struct LapBuffers {
@@ -63,14 +64,21 @@ struct LapBuffers {
     int *owner, *assign, *my_obj, *bwin, *queue;
     unsigned long long *bbest;
     int *sap_pred;    // predecessor row of every column after a search
+    int *tflag, *tlist, *mark_row, *mark_col;  // augmenting-path targets and the vertices used
+    i64 *ufree;       // potentials of the free rows
+    i64 *mben;        // benefit a~ of every assigned row's pair
     int *frow[2];     // frontier lists (rows to scan) of alternate epochs
     i64 *fh[2];       // their label offsets
+    int *fj0[2];      // their boosted columns (-1: none)
+    i64 *fdl[2];      // and boosts
     SapSlot *ring;    // 4 reduction slots
 };
 
 size_t lap_bytes(int n, int /*nchunks*/) {
     return 2 * (size_t)n * sizeof(i64) + 5 * (size_t)n * sizeof(int) + (size_t)n * 8 + 16 * 256 +
-           (size_t)n * sizeof(int) + 2 * (size_t)n * (sizeof(int) + sizeof(i64)) + 4 * sizeof(SapSlot) + 6 * 256;
+           (size_t)n * sizeof(int) + 2 * (size_t)n * (sizeof(int) + sizeof(i64)) + 4 * sizeof(SapSlot) + 6 * 256 +
+           4 * (size_t)n * sizeof(int) + 2 * (size_t)n * sizeof(i64) + 6 * 256 +
+           2 * (size_t)n * (sizeof(int) + sizeof(i64)) + 4 * 256;
 }
 
 static LapBuffers carve(void *base, int n) {
@@ -94,7 +102,17 @@ static LapBuffers carve(void *base, int n) {
     L.frow[1] = (int *)take(sizeof(int) * n);
     L.fh[0] = (i64 *)take(sizeof(i64) * n);
     L.fh[1] = (i64 *)take(sizeof(i64) * n);
+    L.fj0[0] = (int *)take(sizeof(int) * n);
+    L.fj0[1] = (int *)take(sizeof(int) * n);
+    L.fdl[0] = (i64 *)take(sizeof(i64) * n);
+    L.fdl[1] = (i64 *)take(sizeof(i64) * n);
     L.ring = (SapSlot *)take(4 * sizeof(SapSlot));
+    L.tflag = (int *)take(sizeof(int) * n);
+    L.tlist = (int *)take(sizeof(int) * n);
+    L.mark_row = (int *)take(sizeof(int) * n);
+    L.mark_col = (int *)take(sizeof(int) * n);
+    L.ufree = (i64 *)take(sizeof(i64) * n);
+    L.mben = (i64 *)take(sizeof(i64) * n);
     return L;
 }
 
@@ -104,17 +122,29 @@ int lap_chunks(int) { return 1; }
 struct Quant {
     float mul;  // sgn * 2^(40 - e): an exact power-of-two scaling
     i64 qm;     // Qm
+    int qsh;    // log2 Qm
 };
 
-__device__ __forceinline__ i64 benefit(float m, const Quant q) { return __float2ll_rn(m * q.mul) * q.qm; }
+__device__ __forceinline__ i64 benefit(float m, const Quant q) {
+    return (i64)((unsigned long long)__float2ll_rn(m * q.mul) << q.qsh);  // round(m 2^(40-e)) * Qm
+}
 
 constexpr i64 kNegInf = LLONG_MIN / 4;
 
 // ---------------------------------------------------------------- scans
 
-// Top-2 of v_j = a_ij - p_j over j = first, first + stride, ... < n, 8 loads in flight.
+// Ties between objects are broken by the key (j - i) mod n of bidder i: the first
+// tied object at or after column i.  Rows with identical benefits then spread over
+// a tied block of objects instead of all bidding for its lowest column (any tie
+// rule leaves the auction exact).  j1 holds that key until tie_key_to_col.
+__device__ __forceinline__ int col_to_tie_key(int j, int i, int n) { return j >= i ? j - i : j - i + n; }
+__device__ __forceinline__ int tie_key_to_col(int k, int i, int n) { return k + i < n ? k + i : k + i - n; }
+
+// Top-2 of v_j = a_ij - p_j over j = first, first + stride, ... < n, 8 loads in
+// flight; j1 is the tie key of the best object of bidder `row`.
 __device__ __forceinline__ void top2_scan(const float *__restrict__ Mi, const i64 *__restrict__ price, int n,
-                                          const Quant q, int first, int stride, i64 &b1, i64 &b2, int &j1) {
+                                          const Quant q, int first, int stride, int row, i64 &b1, i64 &b2,
+                                          int &j1) {
     constexpr int U = 8;
     for (int base = first; base < n; base += U * stride) {
         float m[U];
@@ -130,10 +160,11 @@ __device__ __forceinline__ void top2_scan(const float *__restrict__ Mi, const i6
             const int j = base + u * stride;
             if (j < n) {
                 const i64 v = benefit(m[u], q) - pr[u];
-                if (v > b1) {
+                const int k = col_to_tie_key(j, row, n);
+                if (v > b1 || (v == b1 && k < j1)) {
                     b2 = b1;
                     b1 = v;
-                    j1 = j;
+                    j1 = k;
                 } else if (v > b2) {
                     b2 = v;
                 }
@@ -191,7 +222,7 @@ __global__ void __launch_bounds__(256) k_lap_bid(const float *__restrict__ M, in
         }
         i64 b1 = kNegInf, b2 = kNegInf;
         int j1 = INT_MAX;
-        top2_scan(M + (long long)i * n, L.price, n, q, tid, blockDim.x, b1, b2, j1);
+        top2_scan(M + (long long)i * n, L.price, n, q, tid, blockDim.x, i, b1, b2, j1);
         top2_warp(b1, b2, j1);
         if (lane == 0) {
             s_b1[warp] = b1;
@@ -201,6 +232,7 @@ __global__ void __launch_bounds__(256) k_lap_bid(const float *__restrict__ M, in
         __syncthreads();
         if (tid == 0) {
             for (int w = 1; w < nwarps; ++w) top2_merge(b1, b2, j1, s_b1[w], s_b2[w], s_j1[w]);
+            j1 = tie_key_to_col(j1, i, n);
             const i64 inc = (b2 == kNegInf) ? eps : (b1 - b2) + eps;
             const i64 bid = L.price[j1] + inc;
             L.my_obj[i] = j1;
@@ -265,7 +297,7 @@ __global__ void __launch_bounds__(1024) k_lap_tail(const float *__restrict__ M, 
         const int i = L.queue[s_head % n];
         i64 b1 = kNegInf, b2 = kNegInf;
         int j1 = INT_MAX;
-        top2_scan(M + (long long)i * n, L.price, n, q, tid, blockDim.x, b1, b2, j1);
+        top2_scan(M + (long long)i * n, L.price, n, q, tid, blockDim.x, i, b1, b2, j1);
         top2_warp(b1, b2, j1);
         if (lane == 0) {
             s_b1[warp] = b1;
@@ -279,6 +311,7 @@ __global__ void __launch_bounds__(1024) k_lap_tail(const float *__restrict__ M, 
             j1 = lane < nwarps ? s_j1[lane] : INT_MAX;
             top2_warp(b1, b2, j1);
             if (lane == 0) {
+                j1 = tie_key_to_col(j1, i, n);
                 const i64 inc = (b2 == kNegInf) ? eps : (b1 - b2) + eps;
                 L.price[j1] += inc;
                 const int old = L.owner[j1];
@@ -404,10 +437,11 @@ __global__ void __cluster_dims__(LAP_CLUSTER, 1, 1) __launch_bounds__(256)
             for (int u = 0; u < 4; ++u) {
                 const int jj = j + u * blockDim.x;
                 const i64 v = benefit(v4[u], q) - price_s[jj - c0];
-                if (v > b1) {
+                const int k = col_to_tie_key(jj, i, n);
+                if (v > b1 || (v == b1 && k < j1)) {
                     b2 = b1;
                     b1 = v;
-                    j1 = jj;
+                    j1 = k;
                 } else if (v > b2) {
                     b2 = v;
                 }
@@ -415,10 +449,11 @@ __global__ void __cluster_dims__(LAP_CLUSTER, 1, 1) __launch_bounds__(256)
         }
         for (; j < c1; j += blockDim.x) {
             const i64 v = benefit(__ldg(Mi + j), q) - price_s[j - c0];
-            if (v > b1) {
+            const int k = col_to_tie_key(j, i, n);
+            if (v > b1 || (v == b1 && k < j1)) {
                 b2 = b1;
                 b1 = v;
-                j1 = j;
+                j1 = k;
             } else if (v > b2) {
                 b2 = v;
             }
@@ -442,6 +477,7 @@ __global__ void __cluster_dims__(LAP_CLUSTER, 1, 1) __launch_bounds__(256)
             b2 = s_b2[0];
             j1 = s_j1[0];
             for (int r = 1; r < LAP_CLUSTER; ++r) top2_merge(b1, b2, j1, s_b1[r], s_b2[r], s_j1[r]);
+            j1 = tie_key_to_col(j1, i, n);
             const i64 inc = (b2 == kNegInf) ? eps : (b1 - b2) + eps;
             const int ro = j1 / W, jl = j1 - ro * W;
             i64 *pp = cluster.map_shared_rank(price_s, ro);
@@ -488,35 +524,47 @@ __global__ void __cluster_dims__(LAP_CLUSTER, 1, 1) __launch_bounds__(256)
 
 // Slack of every assigned row, delta_i = max_j (a_ij - p_j) - (a_i,j_i - p_j_i) >= 0,
 // into my_bid[i], and its object into my_obj[i] (the pairs whose benefit a~ adds
-// delta_i); the unassigned rows are listed in queue[0, lap_free).  One warp per row.
+// delta_i); every unassigned row gets the potential u_i = -max_j (a_ij - p_j) in
+// ufree[i] and is listed in queue[0, lap_free).  One CTA per row.
 __global__ void __launch_bounds__(256) k_lap_sap_prep(const float *__restrict__ M, int n, const Quant q,
                                                       const LapBuffers L, DevState *st) {
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    for (int i = gw; i < n; i += nw) {
+    __shared__ i64 s_b1[8], s_b2[8];
+    __shared__ int s_j1[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
         const int ji = L.assign[i];
-        if (ji < 0) {
-            if (lane == 0) {
-                L.my_obj[i] = -1;
-                L.my_bid[i] = 0;
-                L.queue[atomicAdd(&st->lap_free, 1)] = i;
-            }
-            continue;
-        }
         const float *Mi = M + (long long)i * n;
         i64 b1 = kNegInf, b2 = kNegInf;
         int j1 = INT_MAX;
-        top2_scan(Mi, L.price, n, q, lane, 32, b1, b2, j1);
+        top2_scan(Mi, L.price, n, q, tid, blockDim.x, i, b1, b2, j1);
         top2_warp(b1, b2, j1);
         if (lane == 0) {
-            const i64 d = b1 - (benefit(Mi[ji], q) - L.price[ji]);
-            L.my_obj[i] = ji;
-            L.my_bid[i] = d > 0 ? d : 0;
+            s_b1[warp] = b1;
+            s_b2[warp] = b2;
+            s_j1[warp] = j1;
         }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < nwarps; ++w) top2_merge(b1, b2, j1, s_b1[w], s_b2[w], s_j1[w]);
+            if (ji < 0) {
+                L.my_obj[i] = -1;
+                L.my_bid[i] = 0;
+                L.ufree[i] = -b1;
+                L.queue[atomicAdd(&st->lap_free, 1)] = i;
+            } else {
+                const i64 a = benefit(Mi[ji], q);
+                const i64 d = b1 - (a - L.price[ji]);
+                L.my_obj[i] = ji;
+                L.my_bid[i] = d > 0 ? d : 0;
+                L.mben[i] = a + (d > 0 ? d : 0);
+            }
+        }
+        __syncthreads();
     }
 }
 
 constexpr int SAP_THREADS = 256;
+constexpr int SAP_STEP = 256;  // open columns settled per parallel step (more on exact ties)
 constexpr i64 kPosInf = LLONG_MAX / 4;
 
 // Reduced cost of (i, j) in the minimisation form: c~_ij = -a~_ij, the benefit of
@@ -555,18 +603,22 @@ __device__ __forceinline__ void block_argmin(i64 &x, int &j, i64 *sx, int *sj) {
 // GPU (a cooperative launch; every thread owns CPT columns, j = global thread +
 // c * total threads, and keeps their dual v_j = -p_j, label d_j, predecessor row,
 // owner and state -- open, in the current bucket, or closed -- in registers).
-// One search per row, Dijkstra by label buckets: all open columns with a label
-// <= mu + Delta (mu the least open label) join the bucket; the rows owning them are
-// scanned in parallel (each thread relaxes its columns over the listed rows), and
-// bucket columns whose label drops are scanned again, until the bucket is stable
-// (label-correcting, so the labels are exact whatever Delta).  A free column in a
-// stable bucket ends the search with the least such label (lowest index on ties):
-// the scanned columns' duals move by d_j - d_t and the leader flips the path.  The
-// sequence of results is that of Jonker-Volgenant's sequential Dijkstra; Delta
-// (starting at delta0, widened while buckets stay small) only sets how many rows go
-// into one parallel step.  Control flow depends only on values read after a grid
-// barrier, so every block takes the same path.  At most max_scans row scans per
-// launch; rows left over stay unassigned (lap_unassigned reports them).
+// Hungarian method in Jonker-Volgenant's form: each search starts from all free
+// rows at once (row potentials u_i = min_j (c~_ij - v_j) from the prep kernel;
+// they stay feasible since the duals v only fall) and runs a label-correcting
+// Dijkstra that settles up to SAP_STEP columns per parallel step: the open columns
+// (free columns aside) with the least labels, chosen by a histogram of the labels
+// gathered in the previous step.  Their rows are scanned in parallel (each thread
+// relaxes its columns over the listed rows); a settled column whose label still
+// falls reopens.  Labels only fall from settled labels by non-negative reduced
+// costs, so once the least free-column label d_t is at most every open label, all
+// labels below d_t are final: the settled columns' duals move by d_j - d_t, which
+// makes every shortest augmenting path tight, and the leader CTA flips the paths to
+// all free columns of label d_t (lowest column first) that share no row or column
+// with a path already flipped -- several rows per search where the matrix has
+// ties.  Control flow depends only on values read after a grid barrier, so every
+// block takes the same path.  At most max_scans row scans per launch; rows left
+// over stay unassigned (lap_unassigned reports them).
 template <int CPT>
 __global__ void __launch_bounds__(SAP_THREADS) k_lap_sap_grid(const float *__restrict__ M, int n, const Quant q,
                                                               const LapBuffers L, i64 delta0, long long max_scans,
@@ -579,6 +631,9 @@ __global__ void __launch_bounds__(SAP_THREADS) k_lap_sap_grid(const float *__res
     const bool leader = blockIdx.x == 0 && tid == 0;
     __shared__ i64 s_x[SAP_THREADS / 32];
     __shared__ int s_j[SAP_THREADS / 32];
+    __shared__ int s_scan[SAP_THREADS];
+    __shared__ int s_hist[64];
+    __shared__ long long s_tau, s_nbase;
 
     int col[CPT], pred[CPT], own[CPT];
     i64 v[CPT], d[CPT];
@@ -603,21 +658,24 @@ __global__ void __launch_bounds__(SAP_THREADS) k_lap_sap_grid(const float *__res
             L.ring[k].count = 0;
             L.ring[k].tj = INT_MAX;
         }
+    if (blockIdx.x == 0 && tid < 64)
+        for (int k = 0; k < 4; ++k) L.ring[k].hist[tid] = 0;
     auto barrier = [&]() {
         grid.sync();
         ++e;
+        SapSlot &z = L.ring[(e + 2) & 3];
         if (leader) {
-            SapSlot &z = L.ring[(e + 2) & 3];
             z.minv = kPosInf;
             z.tmin = kPosInf;
             z.count = 0;
             z.tj = INT_MAX;
         }
+        if (blockIdx.x == 0 && tid < 64) z.hist[tid] = 0;
     };
     auto cur = [&]() -> SapSlot & { return L.ring[e & 3]; };
     auto prev = [&]() -> const SapSlot & { return L.ring[(e + 3) & 3]; };
-    // appends (row, h) to this epoch's frontier list, one atomic per warp and column slot
-    auto append = [&](int c, bool want, int row, i64 h) {
+    // appends (row, h) to this epoch's frontier list, one atomic per warp
+    auto append = [&](bool want, int row, i64 h) {
         const unsigned m = __ballot_sync(0xffffffffu, want);
         if (!m) return;
         int base = 0;
@@ -626,184 +684,264 @@ __global__ void __launch_bounds__(SAP_THREADS) k_lap_sap_grid(const float *__res
         base = __shfl_sync(0xffffffffu, base, first);
         if (want) {
             const int k = base + __popc(m & ((1u << lane) - 1u));
+            const int j0 = L.my_obj[row];
             L.frow[e & 1][k] = row;
             L.fh[e & 1][k] = h;
+            L.fj0[e & 1][k] = j0;
+            L.fdl[e & 1][k] = j0 >= 0 ? L.my_bid[row] : 0;
         }
-        (void)c;
     };
-    // label offset h_i = d_j - (c~_ij - v_j) of the row owning column j
-    auto row_offset = [&](int c) -> i64 {
-        const int i = own[c];
-        return d[c] - (sap_cost(M[(long long)i * n + col[c]], q, col[c], L.my_obj[i], L.my_bid[i]) - v[c]);
-    };
-    barrier();
-
-    const int nfree = *(volatile int *)&st->lap_free;
-    long long scans = 0;
-    int solved = 0;
-    bool aborted = false;
-    for (int k = 0; k < nfree && !aborted; ++k) {
-        const int i0 = L.queue[k];
-        {
-            const float *Mi = M + (long long)i0 * n;
-            i64 lmin = kPosInf;
-            int lj = INT_MAX;
+    // label offset h_i = d_j - (c~_ij - v_j) of the row owning column j (c~_ij = -mben[i])
+    auto row_offset = [&](int c) -> i64 { return d[c] + L.mben[own[c]] + v[c]; };
+    // statistics of the open columns for the next step, into this epoch's slot: the
+    // least free-column label, the least open non-free label and the histogram of
+    // the open non-free labels by bit length of (label - base)
+    auto step_stats = [&](i64 base) {
+        if (tid < 64) s_hist[tid] = 0;
+        i64 lt = kPosInf, lm = kPosInf;
+        int dummy = INT_MAX;
+        __syncthreads();
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) {
-                if (col[c] < n) {
-                    d[c] = sap_cost(__ldg(Mi + col[c]), q, col[c], -1, 0) - v[c];
-                    pred[c] = i0;
-                    stt[c] = 0;
-                    if (d[c] < lmin) lmin = d[c];
-                }
+        for (int c = 0; c < CPT; ++c) {
+            if (col[c] >= n || stt[c] != 0) continue;
+            if (own[c] < 0) {
+                if (d[c] < lt) lt = d[c];
+            } else {
+                if (d[c] < lm) lm = d[c];
+                const long long x = d[c] - base;  // >= 0 (base is a lower bound)
+                atomicAdd(&s_hist[x <= 0 ? 0 : min(63, 64 - __clzll(x))], 1);
             }
-            block_argmin(lmin, lj, s_x, s_j);
-            if (tid == 0) atomicMin(&cur().minv, lmin);
         }
-        barrier();
-        i64 mu = prev().minv;
-        i64 Delta = delta0 > 0 ? delta0 : 1;
-        int t = -1;
-        i64 dt = 0;
-        while (true) {  // buckets
-            if (mu >= kPosInf) {  // no open column left: cannot happen while a row is free
-                aborted = true;
-                break;
+        block_argmin(lt, dummy, s_x, s_j);
+        if (tid == 0) atomicMin(&cur().tmin, lt);
+        dummy = INT_MAX;
+        block_argmin(lm, dummy, s_x, s_j);
+        if (tid == 0) atomicMin(&cur().minv, lm);
+        if (tid < 64 && s_hist[tid]) atomicAdd(&cur().hist[tid], s_hist[tid]);
+    };
+    // the widest bound tau = base + 2^b - 1 taking in at most SAP_STEP open non-free
+    // columns (never none), capped below the least free label; nbase = the lower edge
+    // of the lowest non-empty histogram bin, a lower bound of every label from now on
+    auto choose_tau = [&](i64 base, i64 tmin, i64 *tau, i64 *nbase) {
+        if (tid == 0) {
+            const int *h = prev().hist;
+            int cum = 0, best = -1, first = -1;
+            for (int b = 0; b < 64; ++b) {
+                cum += h[b];
+                if (h[b] && first < 0) first = b;
+                if (cum <= SAP_STEP) best = b;
             }
-            const i64 tau = mu > kPosInf - Delta ? kPosInf : mu + Delta;
+            if (first < 0) first = 0;
+            if (best < first) best = first;
+            const i64 w = best >= 62 ? kPosInf : (1LL << best) - 1;
+            i64 t = w >= kPosInf - 1 - base ? kPosInf - 1 : base + w;
+            if (t > tmin - 1) t = tmin - 1;
+            s_tau = t;
+            s_nbase = base + (first > 0 ? (1LL << (first - 1)) : 0);
+        }
+        __syncthreads();
+        *tau = s_tau;
+        *nbase = s_nbase;
+    };
+    // relaxes the thread's columns over rows[0, cnt) (offsets hs[r], or -ufree[row]
+    // for the free rows when hs is null); ch[c] says whether d[c] fell
+    // (the free rows when hs is null: offset -ufree[row], no boost; else the list's
+    // offsets, boosted columns and boosts); every load of a batch of rows is issued
+    // before any of them is used
+    auto relax = [&](const int *rows_in, const i64 *hs, const int *j0s, const i64 *dls, int cnt, bool *ch) {
+        constexpr int RU = CPT >= 8 ? 4 : 32 / CPT;  // rows in flight: 32 loads per thread
+        for (int r0 = 0; r0 < cnt; r0 += RU) {
+            int rows[RU], jj0[RU];
+            float m[RU][CPT];
+            i64 hh[RU], ddl[RU];
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) {
-                const bool in = col[c] < n && stt[c] == 0 && d[c] <= tau;
-                if (in) stt[c] = 1;
-                const bool want = in && own[c] >= 0;
-                append(c, want, want ? own[c] : 0, want ? row_offset(c) : 0);
+            for (int u = 0; u < RU; ++u) {
+                const bool ok = r0 + u < cnt;
+                rows[u] = ok ? rows_in[r0 + u] : -1;
+                jj0[u] = ok && hs ? j0s[r0 + u] : -1;
+                ddl[u] = ok && hs ? dls[r0 + u] : 0;
+                hh[u] = ok && hs ? hs[r0 + u] : 0;
             }
-            barrier();
-            int cnt = prev().count;
-            long long bucket_scans = 0;
-            while (cnt > 0) {  // relaxations until the bucket is stable
-                scans += cnt;
-                bucket_scans += cnt;
-                if (scans > max_scans) {
-                    aborted = true;
-                    break;
-                }
-                const int *fr = L.frow[(e + 1) & 1];
-                const i64 *fh = L.fh[(e + 1) & 1];
-                bool ch[CPT];
 #pragma unroll
-                for (int c = 0; c < CPT; ++c) ch[c] = false;
-                constexpr int RU = CPT >= 8 ? 2 : 16 / CPT;  // rows in flight: 16 loads per thread
-                for (int r0 = 0; r0 < cnt; r0 += RU) {
-                    int rows[RU];
-                    float m[RU][CPT];
+            for (int u = 0; u < RU; ++u) {
 #pragma unroll
-                    for (int u = 0; u < RU; ++u) {
-                        rows[u] = r0 + u < cnt ? fr[r0 + u] : -1;
+                for (int c = 0; c < CPT; ++c)
+                    m[u][c] = (rows[u] >= 0 && col[c] < n) ? __ldg(M + (long long)rows[u] * n + col[c]) : 0.f;
+                if (!hs && rows[u] >= 0) hh[u] = -L.ufree[rows[u]];
+            }
 #pragma unroll
-                        for (int c = 0; c < CPT; ++c)
-                            m[u][c] = (rows[u] >= 0 && col[c] < n) ? __ldg(M + (long long)rows[u] * n + col[c]) : 0.f;
-                    }
+            for (int u = 0; u < RU; ++u) {
+                if (rows[u] < 0) break;
+                const i64 h = hh[u];
+                const int j0 = jj0[u];
+                const i64 dl = ddl[u];
 #pragma unroll
-                    for (int u = 0; u < RU; ++u) {
-                        if (rows[u] < 0) break;
-                        const i64 h = fh[r0 + u];
-                        const int j0 = L.my_obj[rows[u]];
-                        const i64 dl = L.my_bid[rows[u]];
-#pragma unroll
-                        for (int c = 0; c < CPT; ++c) {
-                            if (col[c] < n && stt[c] != 2) {
-                                const i64 nd = h + sap_cost(m[u][c], q, col[c], j0, dl) - v[c];
-                                if (nd < d[c]) {
-                                    d[c] = nd;
-                                    pred[c] = rows[u];
-                                    ch[c] = true;
-                                }
-                            }
+                for (int c = 0; c < CPT; ++c) {
+                    if (col[c] < n) {  // settled columns too: a lower label reopens them
+                        const i64 nd = h + sap_cost(m[u][c], q, col[c], j0, dl) - v[c];
+                        if (nd < d[c]) {
+                            d[c] = nd;
+                            pred[c] = rows[u];
+                            ch[c] = true;
                         }
                     }
                 }
-#pragma unroll
-                for (int c = 0; c < CPT; ++c) {
-                    if (ch[c] && stt[c] == 0 && d[c] <= tau) stt[c] = 1;
-                    const bool want = ch[c] && stt[c] == 1 && own[c] >= 0;
-                    append(c, want, want ? own[c] : 0, want ? row_offset(c) : 0);
-                }
-                barrier();
-                cnt = prev().count;
-            }
-            if (aborted) break;
-            // the bucket is stable: its free columns end the search, else it closes
-            i64 lt = kPosInf, lm = kPosInf;
-            int dummy = INT_MAX;
-#pragma unroll
-            for (int c = 0; c < CPT; ++c) {
-                if (col[c] >= n) continue;
-                if (stt[c] == 1 && own[c] < 0 && d[c] < lt) lt = d[c];
-                if (stt[c] == 0 && d[c] < lm) lm = d[c];
-            }
-            block_argmin(lt, dummy, s_x, s_j);
-            if (tid == 0) atomicMin(&cur().tmin, lt);
-            dummy = INT_MAX;
-            block_argmin(lm, dummy, s_x, s_j);
-            if (tid == 0) atomicMin(&cur().minv, lm);
-            barrier();
-            const i64 tm = prev().tmin;
-            if (tm < kPosInf) {
-                int lj = INT_MAX;
-                i64 z = 0;
-#pragma unroll
-                for (int c = 0; c < CPT; ++c)
-                    if (col[c] < n && stt[c] == 1 && own[c] < 0 && d[c] == tm && col[c] < lj) lj = col[c];
-                block_argmin(z, lj, s_x, s_j);
-                if (tid == 0) atomicMin(&cur().tj, lj);
-                barrier();
-                t = prev().tj;
-                dt = tm;
-                break;
-            }
-            mu = prev().minv;
-#pragma unroll
-            for (int c = 0; c < CPT; ++c)
-                if (stt[c] == 1) stt[c] = 2;
-            if (bucket_scans < 32) {
-                Delta = Delta > (kPosInf >> 3) ? kPosInf : Delta * 4;
-            } else if (bucket_scans > 8192 && Delta / 2 >= (delta0 > 0 ? delta0 : 1)) {
-                Delta /= 2;
             }
         }
-        if (aborted || t < 0 || t >= n) {
+    };
+    barrier();
+
+    const int nfree0 = *(volatile int *)&st->lap_free;
+    int nfree = nfree0;  // rows still free, listed in queue[0, nfree) (kept up to date by the leader)
+    long long scans = 0;
+    int searches = 0;
+    bool aborted = false;
+    while (nfree > 0 && !aborted) {
+        ++searches;
+        // labels from all free rows at once, then the statistics for the first step
+        i64 base = 0;  // a lower bound of every open label (all labels are reduced costs, >= 0)
+        {
+            bool ch[CPT];
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                ch[c] = false;
+                d[c] = kPosInf;
+                pred[c] = -1;
+                stt[c] = col[c] < n ? 0 : 2;
+            }
+            relax(L.queue, nullptr, nullptr, nullptr, nfree, ch);
+            scans += nfree;
+            step_stats(base);
+        }
+        barrier();
+        i64 dt = 0;
+        bool found = false;
+        while (true) {
+            // (1) the free columns' least label ends the search once no open non-free
+            // column lies below it; else the least open non-free labels are settled
+            const i64 tmin = prev().tmin, minv = prev().minv;
+            if (tmin <= minv) {
+                if (tmin >= kPosInf) {
+                    aborted = true;  // no column reachable: cannot happen while a row is free
+                } else {
+                    dt = tmin;
+                    found = true;
+                }
+                break;
+            }
+            i64 tau, nbase;
+            choose_tau(base, tmin, &tau, &nbase);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const bool in = col[c] < n && stt[c] == 0 && own[c] >= 0 && d[c] <= tau;
+                if (in) stt[c] = 2;
+                append(in, in ? own[c] : 0, in ? row_offset(c) : 0);
+            }
+            base = nbase;
+            barrier();
+            // (2) scan the settled columns' rows; settled columns whose label falls reopen
+            const int cnt = prev().count;
+            scans += cnt;
+            if (scans > max_scans) {  // uniform: every block adds the same counts
+                aborted = true;
+                break;
+            }
+            bool ch[CPT];
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) ch[c] = false;
+            const int pb = (e + 1) & 1;
+            relax(L.frow[pb], L.fh[pb], L.fj0[pb], L.fdl[pb], cnt, ch);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c)
+                if (ch[c] && stt[c] == 2) stt[c] = 0;
+            step_stats(base);
+            barrier();
+        }
+        if (aborted || !found) {
             aborted = true;
             break;
         }
-        // duals of the settled columns; predecessors for the path walk
+        // duals of the settled columns; predecessors and the targets (free columns of
+        // label d_t) for the leader CTA
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
             if (col[c] < n) {
-                if (stt[c] != 0 && d[c] < dt) v[c] += d[c] - dt;
+                if (stt[c] == 2 && d[c] < dt) v[c] += d[c] - dt;
                 L.sap_pred[col[c]] = pred[c];
+                if (own[c] < 0 && d[c] == dt) L.tflag[col[c]] = searches;
             }
         barrier();
-        if (leader) {
-            int j = t;
-            for (int hop = 0; hop <= n; ++hop) {
-                const int i = L.sap_pred[j];
-                if (i < 0 || i >= n) {
-                    st->error = GOAT_ERR_NOT_CONVERGED;
-                    break;
+        if (blockIdx.x == 0) {
+            // targets in column order: block-wide compaction of the flagged columns
+            const int chunk = (n + SAP_THREADS - 1) / SAP_THREADS;
+            const int j0 = tid * chunk, j1 = min(n, j0 + chunk);
+            int cntf = 0;
+            for (int j = j0; j < j1; ++j) cntf += L.tflag[j] == searches;
+            s_scan[tid] = cntf;
+            __syncthreads();
+            for (int o = 1; o < SAP_THREADS; o <<= 1) {  // inclusive scan
+                const int add = tid >= o ? s_scan[tid - o] : 0;
+                __syncthreads();
+                s_scan[tid] += add;
+                __syncthreads();
+            }
+            int at = s_scan[tid] - cntf;
+            for (int j = j0; j < j1; ++j)
+                if (L.tflag[j] == searches) L.tlist[at++] = j;
+            const int ntarg = s_scan[SAP_THREADS - 1];
+            __syncthreads();
+            if (tid == 0) {
+                const int stamp = searches;
+                int placed = 0;
+                for (int k = 0; k < ntarg; ++k) {
+                    // check the path: no row or column already used by this search
+                    bool ok = true;
+                    int j = L.tlist[k];
+                    for (int hop = 0; hop <= n; ++hop) {
+                        const int i = L.sap_pred[j];
+                        if (i < 0 || i >= n || L.mark_col[j] == stamp || L.mark_row[i] == stamp) {
+                            ok = false;
+                            break;
+                        }
+                        const int jn = L.assign[i];
+                        if (jn < 0) break;
+                        j = jn;
+                    }
+                    if (!ok) continue;
+                    j = L.tlist[k];
+                    for (int hop = 0; hop <= n; ++hop) {
+                        const int i = L.sap_pred[j];
+                        const int jn = L.assign[i];
+                        L.mark_col[j] = stamp;
+                        L.mark_row[i] = stamp;
+                        L.owner[j] = i;
+                        L.assign[i] = j;
+                        L.mben[i] = -sap_cost(M[(long long)i * n + j], q, j, L.my_obj[i], L.my_bid[i]);
+                        if (jn < 0) break;
+                        j = jn;
+                    }
+                    ++placed;
                 }
-                L.owner[j] = i;
-                const int jn = L.assign[i];
-                L.assign[i] = j;
-                if (i == i0 || jn < 0) break;
-                j = jn;
+                // the free rows that are left
+                int m = 0;
+                for (int k = 0; k < nfree; ++k) {
+                    const int i = L.queue[k];
+                    if (L.assign[i] < 0) L.queue[m++] = i;
+                }
+                if (placed == 0) m = -1;  // no path could be flipped: inconsistent state, stop
+                st->lap_free = m;
             }
         }
         barrier();
+        const int left = *(volatile int *)&st->lap_free;
+        if (left < 0) {
+            aborted = true;
+            break;
+        }
+        nfree = left;
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
             if (col[c] < n) own[c] = L.owner[col[c]];
-        ++solved;
     }
 #pragma unroll
     for (int c = 0; c < CPT; ++c)
@@ -812,7 +950,7 @@ __global__ void __launch_bounds__(SAP_THREADS) k_lap_sap_grid(const float *__res
             L.owner[col[c]] = own[c];
         }
     if (leader) {
-        st->lap_unassigned = nfree - solved;
+        st->lap_unassigned = aborted ? (nfree > 0 ? nfree : nfree0) : nfree;
         st->lap_pops += scans;
         st->lap_epochs += e;
     }
@@ -882,7 +1020,7 @@ __global__ void __launch_bounds__(256) k_lap_gap(const float *__restrict__ M, in
         i64 b1 = kNegInf, b2 = kNegInf;
         int j1 = INT_MAX;
         const float *Mi = M + (long long)i * n;
-        top2_scan(Mi, L.price, n, q, lane, 32, b1, b2, j1);
+        top2_scan(Mi, L.price, n, q, lane, 32, i, b1, b2, j1);
         top2_warp(b1, b2, j1);
         if (lane == 0) {
             const int j = L.assign[i];
@@ -964,6 +1102,7 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
     const int bq = std::min(40, 58 - qbits);  // keeps |a_int| and every price far below 2^63
     q.mul = (float)std::ldexp(maximize ? 1.0 : -1.0, bq - e);
     q.qm = 1LL << qbits;
+    q.qsh = qbits;
     const i64 c_int = (1LL << bq) * q.qm;  // bound on |a_int|
 
     k_lap_reset<<<g1, 256, 0, s>>>(n, L, st, 1);
@@ -1039,7 +1178,10 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
             const long long pops =
                 ctl.sap_pops > 0 ? ctl.sap_pops : (last ? 64LL * n + (1LL << 20) : 8LL * n + (1LL << 16));
             cudaMemsetAsync(&st->lap_free, 0, sizeof(int), s);
-            k_lap_sap_prep<<<gbid, 256, 0, s>>>(M, n, q, L, st);
+            cudaMemsetAsync(L.tflag, 0, sizeof(int) * n, s);
+            cudaMemsetAsync(L.mark_row, 0, sizeof(int) * n, s);
+            cudaMemsetAsync(L.mark_col, 0, sizeof(int) * n, s);
+            k_lap_sap_prep<<<growb, 256, 0, s>>>(M, n, q, L, st);
             i64 delta0 = std::max<i64>(1, eps);
             long long max_scans = pops;
             DevState *stp = st;
