@@ -563,8 +563,11 @@ __global__ void __launch_bounds__(256) k_lap_sap_prep(const float *__restrict__ 
     }
 }
 
-constexpr int SAP_THREADS = 256;
-constexpr int SAP_STEP = 256;  // open columns settled per parallel step (more on exact ties)
+constexpr int SAP_SLOTS = 256;                  // column slots per CTA (each CPT columns)
+constexpr int SAP_GROUPS = 2;                   // row groups sharing the slots in a relaxation
+constexpr int SAP_THREADS = SAP_SLOTS * SAP_GROUPS;
+constexpr int SAP_STAGE = 512;                  // frontier entries staged in shared memory at a time
+constexpr int SAP_STEP = 256;                   // open columns settled per parallel step (more on exact ties)
 constexpr i64 kPosInf = LLONG_MAX / 4;
 
 // Reduced cost of (i, j) in the minimisation form: c~_ij = -a~_ij, the benefit of
@@ -573,29 +576,24 @@ __device__ __forceinline__ i64 sap_cost(float m, const Quant q, int j, int j0, i
     return -(benefit(m, q) + (j == j0 ? delta : 0));
 }
 
-// Block-wide minimum of (x, j) pairs, lowest j on ties; the result is valid in thread 0.
-__device__ __forceinline__ void block_argmin(i64 &x, int &j, i64 *sx, int *sj) {
+// Block-wide minima of two values at once; valid in thread 0.
+__device__ __forceinline__ void block_min2(i64 &x, i64 &y, i64 *sx, i64 *sy) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const i64 ox = __shfl_xor_sync(0xffffffffu, x, o);
-        const int oj = __shfl_xor_sync(0xffffffffu, j, o);
-        if (ox < x || (ox == x && oj < j)) {
-            x = ox;
-            j = oj;
-        }
+        x = min(x, (i64)__shfl_xor_sync(0xffffffffu, x, o));
+        y = min(y, (i64)__shfl_xor_sync(0xffffffffu, y, o));
     }
     if (lane == 0) {
         sx[warp] = x;
-        sj[warp] = j;
+        sy[warp] = y;
     }
     __syncthreads();
     if (threadIdx.x == 0)
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-            if (sx[w] < x || (sx[w] == x && sj[w] < j)) {
-                x = sx[w];
-                j = sj[w];
-            }
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            x = min(x, sx[w]);
+            y = min(y, sy[w]);
+        }
     __syncthreads();
 }
 
@@ -626,27 +624,34 @@ __global__ void __launch_bounds__(SAP_THREADS) k_lap_sap_grid(const float *__res
     namespace cg = cooperative_groups;
     cg::grid_group grid = cg::this_grid();
     const int tid = threadIdx.x, lane = tid & 31;
-    const int gthreads = gridDim.x * blockDim.x;
-    const int gt = blockIdx.x * blockDim.x + tid;
+    const int slot = tid % SAP_SLOTS, grp = tid / SAP_SLOTS;
     const bool leader = blockIdx.x == 0 && tid == 0;
-    __shared__ i64 s_x[SAP_THREADS / 32];
-    __shared__ int s_j[SAP_THREADS / 32];
+    __shared__ i64 s_x[SAP_THREADS / 32], s_x2[SAP_THREADS / 32];
     __shared__ int s_scan[SAP_THREADS];
     __shared__ int s_hist[64];
     __shared__ long long s_tau, s_nbase;
+    __shared__ i64 s_v[SAP_SLOTS * CPT];                      // duals of the CTA's columns
+    __shared__ i64 s_cd[SAP_GROUPS - 1][SAP_SLOTS];           // candidates of groups 1.. for one slot set
+    __shared__ int s_cr[SAP_GROUPS - 1][SAP_SLOTS];
+    __shared__ int s_row[SAP_STAGE], s_j0[SAP_STAGE];         // staged frontier entries
+    __shared__ i64 s_h[SAP_STAGE], s_dl[SAP_STAGE];
 
-    int col[CPT], pred[CPT], own[CPT];
+    // Group 0 owns the CTA's columns (state in registers); groups 1.. only help to
+    // scan the frontier rows of a relaxation.  rcol: the column of each slot.
+    int col[CPT], rcol[CPT], pred[CPT], own[CPT];
     i64 v[CPT], d[CPT];
-    unsigned char stt[CPT];  // 0 open, 1 in the bucket, 2 closed
+    unsigned char stt[CPT];  // 0 open, 2 settled
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
-        col[c] = gt + c * gthreads;
+        rcol[c] = blockIdx.x * (SAP_SLOTS * CPT) + c * SAP_SLOTS + slot;
+        col[c] = grp == 0 ? rcol[c] : n;  // n: no column
         const bool ok = col[c] < n;
         v[c] = ok ? -L.price[col[c]] : 0;
         own[c] = ok ? L.owner[col[c]] : -1;
         d[c] = kPosInf;
         pred[c] = -1;
         stt[c] = 2;
+        if (grp == 0) s_v[c * SAP_SLOTS + slot] = v[c];
     }
     // Reduction slots: the one of epoch e (e = barriers passed) is written during e,
     // read during e + 1 and reset by the leader during e + 2 (ring of 4).
@@ -699,7 +704,6 @@ __global__ void __launch_bounds__(SAP_THREADS) k_lap_sap_grid(const float *__res
     auto step_stats = [&](i64 base) {
         if (tid < 64) s_hist[tid] = 0;
         i64 lt = kPosInf, lm = kPosInf;
-        int dummy = INT_MAX;
         __syncthreads();
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
@@ -712,19 +716,21 @@ __global__ void __launch_bounds__(SAP_THREADS) k_lap_sap_grid(const float *__res
                 atomicAdd(&s_hist[x <= 0 ? 0 : min(63, 64 - __clzll(x))], 1);
             }
         }
-        block_argmin(lt, dummy, s_x, s_j);
-        if (tid == 0) atomicMin(&cur().tmin, lt);
-        dummy = INT_MAX;
-        block_argmin(lm, dummy, s_x, s_j);
-        if (tid == 0) atomicMin(&cur().minv, lm);
+        block_min2(lt, lm, s_x, s_x2);
+        if (tid == 0) {
+            atomicMin(&cur().tmin, lt);
+            atomicMin(&cur().minv, lm);
+        }
         if (tid < 64 && s_hist[tid]) atomicAdd(&cur().hist[tid], s_hist[tid]);
     };
     // the widest bound tau = base + 2^b - 1 taking in at most SAP_STEP open non-free
     // columns (never none), capped below the least free label; nbase = the lower edge
     // of the lowest non-empty histogram bin, a lower bound of every label from now on
     auto choose_tau = [&](i64 base, i64 tmin, i64 *tau, i64 *nbase) {
+        if (tid < 64) s_hist[tid] = prev().hist[tid];  // one load per thread, not 64 in a row
+        __syncthreads();
         if (tid == 0) {
-            const int *h = prev().hist;
+            const int *h = s_hist;
             int cum = 0, best = -1, first = -1;
             for (int b = 0; b < 64; ++b) {
                 cum += h[b];
@@ -743,50 +749,88 @@ __global__ void __launch_bounds__(SAP_THREADS) k_lap_sap_grid(const float *__res
         *tau = s_tau;
         *nbase = s_nbase;
     };
-    // relaxes the thread's columns over rows[0, cnt) (offsets hs[r], or -ufree[row]
-    // for the free rows when hs is null); ch[c] says whether d[c] fell
-    // (the free rows when hs is null: offset -ufree[row], no boost; else the list's
-    // offsets, boosted columns and boosts); every load of a batch of rows is issued
-    // before any of them is used
+    // relaxes the CTA's columns over rows[0, cnt) (the free rows when hs is null:
+    // offset -ufree[row], no boost; else the list's offsets, boosted columns and
+    // boosts).  The entries are staged in shared memory; row group g scans entries
+    // g, g + SAP_GROUPS, ... for every slot, and group 0 merges the groups' best
+    // candidates into the labels; ch[c] says whether d[c] fell.
     auto relax = [&](const int *rows_in, const i64 *hs, const int *j0s, const i64 *dls, int cnt, bool *ch) {
-        constexpr int RU = CPT >= 8 ? 4 : 32 / CPT;  // rows in flight: 32 loads per thread
-        for (int r0 = 0; r0 < cnt; r0 += RU) {
-            int rows[RU], jj0[RU];
-            float m[RU][CPT];
-            i64 hh[RU], ddl[RU];
+        constexpr int RU = CPT >= 8 ? 2 : 16 / CPT;  // rows in flight: 16 loads per thread
+        i64 bd[CPT];
+        int br[CPT];
 #pragma unroll
-            for (int u = 0; u < RU; ++u) {
-                const bool ok = r0 + u < cnt;
-                rows[u] = ok ? rows_in[r0 + u] : -1;
-                jj0[u] = ok && hs ? j0s[r0 + u] : -1;
-                ddl[u] = ok && hs ? dls[r0 + u] : 0;
-                hh[u] = ok && hs ? hs[r0 + u] : 0;
+        for (int c = 0; c < CPT; ++c) {
+            bd[c] = kPosInf;
+            br[c] = INT_MAX;
+        }
+        i64 vv[CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) vv[c] = s_v[c * SAP_SLOTS + slot];
+        for (int s0 = 0; s0 < cnt; s0 += SAP_STAGE) {
+            const int len = min(SAP_STAGE, cnt - s0);
+            __syncthreads();  // the previous stage is consumed
+            for (int k = tid; k < len; k += SAP_THREADS) {
+                const int row = rows_in[s0 + k];
+                s_row[k] = row;
+                s_h[k] = hs ? hs[s0 + k] : -L.ufree[row];
+                s_j0[k] = hs ? j0s[s0 + k] : -1;
+                s_dl[k] = hs ? dls[s0 + k] : 0;
             }
+            __syncthreads();
+            for (int r0 = grp; r0 < len; r0 += RU * SAP_GROUPS) {
+                float m[RU][CPT];
 #pragma unroll
-            for (int u = 0; u < RU; ++u) {
+                for (int u = 0; u < RU; ++u) {
+                    const int r = r0 + u * SAP_GROUPS;
 #pragma unroll
-                for (int c = 0; c < CPT; ++c)
-                    m[u][c] = (rows[u] >= 0 && col[c] < n) ? __ldg(M + (long long)rows[u] * n + col[c]) : 0.f;
-                if (!hs && rows[u] >= 0) hh[u] = -L.ufree[rows[u]];
-            }
+                    for (int c = 0; c < CPT; ++c)
+                        m[u][c] = (r < len && rcol[c] < n) ? __ldg(M + (long long)s_row[r] * n + rcol[c]) : 0.f;
+                }
 #pragma unroll
-            for (int u = 0; u < RU; ++u) {
-                if (rows[u] < 0) break;
-                const i64 h = hh[u];
-                const int j0 = jj0[u];
-                const i64 dl = ddl[u];
+                for (int u = 0; u < RU; ++u) {
+                    const int r = r0 + u * SAP_GROUPS;
+                    if (r >= len) break;
+                    const i64 h = s_h[r];
+                    const int j0 = s_j0[r], row = s_row[r];
+                    const i64 dl = s_dl[r];
 #pragma unroll
-                for (int c = 0; c < CPT; ++c) {
-                    if (col[c] < n) {  // settled columns too: a lower label reopens them
-                        const i64 nd = h + sap_cost(m[u][c], q, col[c], j0, dl) - v[c];
-                        if (nd < d[c]) {
-                            d[c] = nd;
-                            pred[c] = rows[u];
-                            ch[c] = true;
+                    for (int c = 0; c < CPT; ++c) {
+                        const i64 nd = h + sap_cost(m[u][c], q, rcol[c], j0, dl) - vv[c];
+                        if (nd < bd[c] || (nd == bd[c] && row < br[c])) {
+                            bd[c] = nd;
+                            br[c] = row;
                         }
                     }
                 }
             }
+        }
+        // merge the groups' candidates, one column set at a time
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            if (grp > 0) {
+                s_cd[grp - 1][slot] = bd[c];
+                s_cr[grp - 1][slot] = br[c];
+            }
+            __syncthreads();
+            if (grp == 0 && col[c] < n) {
+                i64 b = bd[c];
+                int r = br[c];
+#pragma unroll
+                for (int g = 0; g < SAP_GROUPS - 1; ++g) {
+                    const i64 od = s_cd[g][slot];
+                    const int orow = s_cr[g][slot];
+                    if (od < b || (od == b && orow < r)) {
+                        b = od;
+                        r = orow;
+                    }
+                }
+                if (b < d[c]) {
+                    d[c] = b;
+                    pred[c] = r;
+                    ch[c] = true;
+                }
+            }
+            __syncthreads();
         }
     };
     barrier();
@@ -866,7 +910,10 @@ __global__ void __launch_bounds__(SAP_THREADS) k_lap_sap_grid(const float *__res
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
             if (col[c] < n) {
-                if (stt[c] == 2 && d[c] < dt) v[c] += d[c] - dt;
+                if (stt[c] == 2 && d[c] < dt) {
+                    v[c] += d[c] - dt;
+                    s_v[c * SAP_SLOTS + slot] = v[c];
+                }
                 L.sap_pred[col[c]] = pred[c];
                 if (own[c] < 0 && d[c] == dt) L.tflag[col[c]] = searches;
             }
@@ -876,7 +923,8 @@ __global__ void __launch_bounds__(SAP_THREADS) k_lap_sap_grid(const float *__res
             const int chunk = (n + SAP_THREADS - 1) / SAP_THREADS;
             const int j0 = tid * chunk, j1 = min(n, j0 + chunk);
             int cntf = 0;
-            for (int j = j0; j < j1; ++j) cntf += L.tflag[j] == searches;
+#pragma unroll 8
+            for (int j = j0; j < j1; ++j) cntf += __ldcg(L.tflag + j) == searches;
             s_scan[tid] = cntf;
             __syncthreads();
             for (int o = 1; o < SAP_THREADS; o <<= 1) {  // inclusive scan
@@ -1126,7 +1174,7 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
     int sap_cpt = 0, sap_grid = 0;
     if (ctl.sap_pops != 0) {
         for (int c : {1, 2, 4, 8}) {
-            if ((long long)sms * SAP_THREADS * c >= n) {
+            if ((long long)sms * SAP_SLOTS * c >= n) {
                 sap_cpt = c;
                 break;
             }
@@ -1134,7 +1182,7 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
         int coop = 0;
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
         if (!coop) sap_cpt = 0;
-        if (sap_cpt) sap_grid = (int)std::max<int64_t>(1, ceil_div(n, (int64_t)SAP_THREADS * sap_cpt));
+        if (sap_cpt) sap_grid = (int)std::max<int64_t>(1, ceil_div(n, (int64_t)SAP_SLOTS * sap_cpt));
     }
     const bool use_sap = sap_cpt > 0;
     const long long stall = ctl.tail_stall >= 0 ? ctl.tail_stall : std::max(512LL, (long long)n / 32);
