@@ -258,8 +258,10 @@ def test_project_large_matrices(n, kind, mx):
 
 @pytest.mark.parametrize("n", [1, 2, 9, 64, 250])
 def test_project_augmenting_paths_only_integer_bitwise(n):
-    # no bidding at all: every row of every eps phase is placed by the shortest
-    # augmenting path searches; integer matrices with many ties
+    # no bidding at all: every row the auction would bid for is placed by the
+    # shortest augmenting path searches (all of them in the first eps phase, the
+    # rows whose assignment stops being eps-CS in the later ones); integer matrices
+    # with many ties
     rng = np.random.default_rng(100 + n)
     M = rng.integers(0, 20, size=(n, n)).astype(np.float32)
     opts = goat.lap_options(head_rounds=0, tail_bids=0, sap_pops=4 * n * n + 64)
@@ -269,7 +271,7 @@ def test_project_augmenting_paths_only_integer_bitwise(n):
         assert sorted(p) == list(range(n))
         assert cost == oracle.lap(M.astype(np.float64), maximize=mx)[1]
         assert gap == 0.0 and info["filled"] == 0 and info["tail_bids"] == 0
-        assert info["sap_rows"] == n * info["phases"]
+        assert info["sap_rows"] >= n and info["rounds"] == 0
 
 
 @pytest.mark.parametrize("n", [100, 513])
