@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--kernel-case", choices=["gemm", "sinkhorn", "lap", "batched", "warmstart"], default=None,
                     help="run only one step kind a few times on the workload (the small cases profiled with ncu)")
     ap.add_argument("--repeat", type=int, default=3)
+    ap.add_argument("--precision", choices=["bf16", "fp8", "fp32"], default="bf16",
+                    help="form of the products in --kernel-case gemm")
     return ap.parse_args()
 
 
@@ -258,11 +260,13 @@ def run_kernel_case(args):
     out = {"case": args.kernel_case, "n": n}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if args.kernel_case == "gemm":
-        G = goat.goat_gradient(A, B, P)
+        prec = {"bf16": goat.GOAT_PREC_BF16, "fp8": goat.GOAT_PREC_FP8, "fp32": goat.GOAT_PREC_FP32}[args.precision]
+        G = goat.goat_gradient(A, B, P, precision=prec)
         e0.record()
         for _ in range(args.repeat):
-            goat.goat_gradient(A, B, P, out=G)
+            goat.goat_gradient(A, B, P, precision=prec, out=G)
         e1.record()
+        out["precision"] = args.precision
     elif args.kernel_case == "sinkhorn":
         G = goat.goat_gradient(A, B, P)
         eps = 0.03 * float(G.abs().max())

@@ -78,7 +78,12 @@ enum {
     GOAT_PREC_BF16 = 0,
     /* FP32-accurate: every non-adjacency operand is split into two BF16 terms
      * (x = hi + lo), so each product runs twice the BF16 MMA work; error ~1e-6. */
-    GOAT_PREC_FP32 = 1
+    GOAT_PREC_FP32 = 1,
+    /* 8-bit: A, B as E4M3 (exact for 0/1), Q and the intermediate Q B each rounded to
+     * E4M3 under one power-of-two scale per matrix (largest entry near 448), FP32
+     * accumulation; twice the BF16 MMA rate.  (E4M3 x BF16 is not one tensor-core
+     * operation, so Q is 8-bit too.)  Gradient error ~1e-2 relative. */
+    GOAT_PREC_FP8 = 2
 };
 
 #define GOAT_TRACE_MAX 256

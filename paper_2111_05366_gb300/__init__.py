@@ -32,6 +32,7 @@ GOAT_DTYPE_U8 = 0
 GOAT_DTYPE_F32 = 1
 GOAT_PREC_BF16 = 0
 GOAT_PREC_FP32 = 1
+GOAT_PREC_FP8 = 2
 GOAT_TRACE_MAX = 256
 GOAT_MLP_PARAMS = 641
 

@@ -22,7 +22,9 @@ enum : int { NEED_GEMM = 1, NEED_FW = 2, NEED_SK = 4, NEED_LAP = 8, NEED_HOSTCOP
 
 struct Plan {
     size_t state, A16, B16, Xq, C1, GQ, P, G, f, g, deg, partial, lap, perm, Ad, Bd, Id, cost, mlp, total;
-    int ld, terms;
+    size_t A8, B8, Q8, C8, f8s;  // E4M3 operands and their scales (8-bit form)
+    int ld, terms, ld8;
+    bool fp8;
 };
 
 static Plan make_plan(int n, int dtype, int precision, int need) {
@@ -36,7 +38,9 @@ static Plan make_plan(int n, int dtype, int precision, int need) {
     };
     const size_t nn = (size_t)n * (size_t)n;
     w.ld = operand_ld(n);
+    w.ld8 = (int)round_up(n, 128);  // an E4M3 stage holds 128 elements of K
     w.terms = precision == GOAT_PREC_FP32 ? 2 : 1;
+    w.fp8 = precision == GOAT_PREC_FP8;
     w.state = take(sizeof(DevState));
     w.cost = take(16 * sizeof(double));  // [0,3) u64 sums, [3,6) f64 sums, [6] assignment cost, [7,10) LAP bound
     if (need & (NEED_GEMM | NEED_FW)) {
@@ -44,6 +48,13 @@ static Plan make_plan(int n, int dtype, int precision, int need) {
         w.B16 = take((size_t)n * w.ld * 2);
         w.Xq = take((size_t)n * w.terms * w.ld * 2);
         w.C1 = take((size_t)n * w.terms * w.ld * 2);
+        if (w.fp8) {
+            w.A8 = take((size_t)n * w.ld8);
+            w.B8 = take((size_t)n * w.ld8);
+            w.Q8 = take((size_t)n * w.ld8);
+            w.C8 = take((size_t)n * w.ld8);
+            w.f8s = take(4 * sizeof(float));  // [0] max|Q| bits, [1] 1/s_Q, [2] max|C1| bits, [3] 1/s_C1
+        }
     }
     if (need & NEED_FW) {
         w.GQ = take(nn * 4);
@@ -161,9 +172,57 @@ static int cuda_status(cudaError_t e) {
     return e == cudaErrorMemoryAllocation ? GOAT_ERR_OUT_OF_MEMORY : GOAT_ERR_CUDA;
 }
 
+// The 8-bit form of the two products: Q (BF16 in Xq) and then C1 = B Q^T are each
+// rounded to E4M3 under a power-of-two scale; the GEMM epilogues undo the scales.
+static int gradient_fp8(const Plan &w, const Scratch &ws, int n, float *G_out, int *err, cudaStream_t s,
+                        cudaEvent_t between) {
+    float *sc = ws.at<float>(w.f8s);
+    unsigned *amax = reinterpret_cast<unsigned *>(sc);
+    GOAT_TRY(bf16_to_e4m3(ws.at<__nv_bfloat16>(w.Xq), n, w.ld, ws.at<uint8_t>(w.Q8), w.ld8, amax, sc + 1, s));
+    GemmCall c1;
+    std::memset(&c1, 0, sizeof(c1));
+    c1.fp8 = 1;
+    c1.X = ws.at<uint8_t>(w.B8);
+    c1.x_rows = n;
+    c1.x_stride = w.ld8;
+    c1.kx_period = w.ld8;
+    c1.Y = ws.at<uint8_t>(w.Q8);
+    c1.y_rows = n;
+    c1.y_stride = w.ld8;
+    c1.k_total = w.ld8;
+    c1.M = n;
+    c1.N = n;
+    c1.scale = 1.0f;
+    c1.scale_dev = sc + 1;
+    c1.mode = GEMM_OUT_BF16_TERMS;
+    c1.out_b16 = ws.at<__nv_bfloat16>(w.C1);
+    c1.out_terms = 1;
+    c1.term_stride = w.ld;
+    c1.row_stride = w.ld;
+    c1.out_rows = n;
+    c1.out_cols = w.ld;  // the padding columns receive zeros
+    c1.err = err;
+    GOAT_TRY(gemm_xyT(c1, s));
+    if (between) cudaEventRecord(between, s);
+    GOAT_TRY(bf16_to_e4m3(ws.at<__nv_bfloat16>(w.C1), n, w.ld, ws.at<uint8_t>(w.C8), w.ld8,
+                          reinterpret_cast<unsigned *>(sc + 2), sc + 3, s));
+    GemmCall c2 = c1;
+    c2.X = ws.at<uint8_t>(w.A8);
+    c2.Y = ws.at<uint8_t>(w.C8);
+    c2.scale = -2.0f;
+    c2.scale_dev = sc + 3;
+    c2.mode = GEMM_OUT_F32;
+    c2.out_f32 = G_out;
+    c2.ld_out = n;
+    c2.out_b16 = nullptr;
+    c2.out_cols = n;
+    return gemm_xyT(c2, s);
+}
+
 // -grad f(X) = -2 A X B for symmetric A, B, with X already in the split-term buffer Xq.
 static int gradient_from_terms(const Plan &w, const Scratch &ws, int n, float *G_out, int *err, cudaStream_t s,
                                cudaEvent_t between = nullptr) {
+    if (w.fp8) return gradient_fp8(w, ws, n, G_out, err, s, between);
     GemmCall c1;
     std::memset(&c1, 0, sizeof(c1));
     c1.X = ws.at<__nv_bfloat16>(w.B16);
@@ -204,6 +263,10 @@ static int prepare_operands(const void *A, const void *B, int n, int dtype, cons
                             DevState *st, float *degA, float *degB, int *pinned, cudaStream_t s) {
     GOAT_TRY(adj_to_bf16(A, dtype, n, ws.at<__nv_bfloat16>(w.A16), w.ld, degA, s));
     GOAT_TRY(adj_to_bf16(B, dtype, n, ws.at<__nv_bfloat16>(w.B16), w.ld, degB, s));
+    if (w.fp8) {
+        GOAT_TRY(adj_to_e4m3(A, dtype, n, ws.at<uint8_t>(w.A8), w.ld8, s));
+        GOAT_TRY(adj_to_e4m3(B, dtype, n, ws.at<uint8_t>(w.B8), w.ld8, s));
+    }
     GOAT_TRY(count_asym(A, dtype, n, &st->asym_count, s));
     GOAT_TRY(count_asym(B, dtype, n, &st->asym_count, s));
     GOAT_TRY(cuda_status(cudaMemcpyAsync(pinned, &st->asym_count, sizeof(int), cudaMemcpyDeviceToHost, s)));
@@ -419,7 +482,7 @@ static goat_params resolve_params(const goat_params *p) {
     return r;
 }
 
-static bool valid_precision(int p) { return p == GOAT_PREC_BF16 || p == GOAT_PREC_FP32; }
+static bool valid_precision(int p) { return p == GOAT_PREC_BF16 || p == GOAT_PREC_FP32 || p == GOAT_PREC_FP8; }
 static bool valid_dtype(int d) { return d == GOAT_DTYPE_U8 || d == GOAT_DTYPE_F32; }
 
 }  // namespace goat

@@ -3,6 +3,8 @@
 // reductions (K3), the update (K4) and the objective at a permutation.
 #include <algorithm>
 
+#include <cuda_fp8.h>
+
 #include "goat_common.cuh"
 #include "goat_internal.h"
 
@@ -27,6 +29,62 @@ __global__ void __launch_bounds__(256) k_adj_to_bf16(const T *__restrict__ A, in
         }
         s = warp_sum(s);
         if (lane == 0 && deg) deg[i] = s;
+    }
+}
+
+// ---------------------------------------------------------------- 8-bit operands
+
+// Two floats -> two E4M3 bytes (round to nearest, saturating at +-448).
+__device__ __forceinline__ unsigned short e4m3x2(float a, float b) {
+    return (unsigned short)__nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+}
+
+// Adjacency (uint8 or float32, dense ld n) -> E4M3 GEMM operand, row stride ld8,
+// zero padding.  0/1 entries are exact (1.0 = 0x38); other weights round to E4M3.
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_to_e4m3(const T *__restrict__ A, int n, uint8_t *__restrict__ A8,
+                                                     int ld8) {
+    const int pairs = ld8 / 2;
+    const long long total = (long long)n * pairs;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / pairs), j = (int)(t - (long long)i * pairs) * 2;
+        const T *src = A + (long long)i * n;
+        const float a = j < n ? (float)src[j] : 0.0f, b = j + 1 < n ? (float)src[j + 1] : 0.0f;
+        *reinterpret_cast<unsigned short *>(A8 + (long long)i * ld8 + j) = e4m3x2(a, b);
+    }
+}
+
+// max |x| of a BF16 matrix (non-negative float bits, atomicMax).
+__global__ void __launch_bounds__(256) k_absmax_bf16(const __nv_bfloat16 *__restrict__ X, long long total,
+                                                     unsigned *out) {
+    float m = 0.0f;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(__bfloat162float(X[t])));
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(out, __float_as_uint(m));
+}
+
+// BF16 matrix (rows x ld_src) -> E4M3 (rows x ld8, zero padding) scaled by s, the
+// largest power of two with s max|x| <= 448; inv_scale <- 1 / s (exact).
+__global__ void __launch_bounds__(256) k_bf16_to_e4m3(const __nv_bfloat16 *__restrict__ X, int rows, int ld_src,
+                                                      uint8_t *__restrict__ X8, int ld8, const unsigned *amax_bits,
+                                                      float *inv_scale) {
+    const float amax = __uint_as_float(*amax_bits);
+    // power of two at or below 448 / amax: keep the exponent bits of the quotient
+    const float q = amax > 0.0f ? 448.0f / amax : 1.0f;
+    const float sc = __uint_as_float(__float_as_uint(q) & 0x7F800000u);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *inv_scale = 1.0f / sc;
+    const int pairs = ld8 / 2;
+    const long long total = (long long)rows * pairs;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / pairs), j = (int)(t - (long long)i * pairs) * 2;
+        const __nv_bfloat16 *src = X + (long long)i * ld_src;
+        const float a = j < ld_src ? __bfloat162float(src[j]) * sc : 0.0f;
+        const float b = j + 1 < ld_src ? __bfloat162float(src[j + 1]) * sc : 0.0f;
+        *reinterpret_cast<unsigned short *>(X8 + (long long)i * ld8 + j) = e4m3x2(a, b);
     }
 }
 
@@ -406,6 +464,26 @@ int adj_to_bf16(const void *A, int dtype, int n, __nv_bfloat16 *A16, int ld16, f
         k_adj_to_bf16<uint8_t><<<grid, 256, 0, s>>>((const uint8_t *)A, n, A16, ld16, deg);
     else
         k_adj_to_bf16<float><<<grid, 256, 0, s>>>((const float *)A, n, A16, ld16, deg);
+    return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
+}
+
+int adj_to_e4m3(const void *A, int dtype, int n, uint8_t *A8, int ld8, cudaStream_t s) {
+    note_launches(1);
+    const int grid = grid_for((long long)n * (ld8 / 2));
+    if (dtype == GOAT_DTYPE_U8)
+        k_adj_to_e4m3<uint8_t><<<grid, 256, 0, s>>>((const uint8_t *)A, n, A8, ld8);
+    else
+        k_adj_to_e4m3<float><<<grid, 256, 0, s>>>((const float *)A, n, A8, ld8);
+    return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
+}
+
+int bf16_to_e4m3(const __nv_bfloat16 *X, int rows, int ld_src, uint8_t *X8, int ld8, unsigned *amax_bits,
+                 float *inv_scale, cudaStream_t s) {
+    note_launches(2);
+    cudaMemsetAsync(amax_bits, 0, sizeof(unsigned), s);
+    k_absmax_bf16<<<grid_for((long long)rows * ld_src), 256, 0, s>>>(X, (long long)rows * ld_src, amax_bits);
+    k_bf16_to_e4m3<<<grid_for((long long)rows * (ld8 / 2)), 256, 0, s>>>(X, rows, ld_src, X8, ld8, amax_bits,
+                                                                         inv_scale);
     return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
 }
 

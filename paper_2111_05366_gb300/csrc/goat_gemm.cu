@@ -13,9 +13,15 @@
 // (Y = [Y_hi | Y_lo] along K, X re-read for each term): that is how the
 // FP32-accurate form adds A Q_hi B + A Q_lo B in one TMEM accumulator.
 //
+// The same kernel runs the 8-bit form (FP8 = true): E4M3 operands, kind::f8f6f4.
+// A stage then holds 128 elements of K instead of 64 -- the same 128 bytes per
+// swizzled row, so the shared-memory layout, the descriptors and their 32-byte K
+// steps are unchanged; only the element type, the K extent per stage and the
+// instruction kind differ.
+//
 // Kernel structure (one persistent CTA per SM, 192 threads):
-//   warp 0      TMA producer: X tile 128x64 and Y tile 256x64 per stage, 4 stages
-//   warp 1      TMEM owner and MMA issuer: 4 x tcgen05.mma M=128 N=256 K=16 per stage
+//   warp 0      TMA producer: X tile 128x64 and Y tile 256x64 per stage (BF16), 4 stages
+//   warp 1      TMEM owner and MMA issuer: 4 x tcgen05.mma M=128 N=256 K=16 (K=32 for E4M3) per stage
 //   warps 2-5   epilogue: tcgen05.ld 32 lanes x 32 columns, scale, convert, store
 // Two TMEM accumulators (2 x 256 columns) let the epilogue of tile t overlap
 // the MMAs of tile t+1.  Every wait is bounded (see mbar_wait_bounded).
@@ -43,6 +49,7 @@ struct GemmParams {
     int num_kb;          // K extent / BK
     int tiles_m, tiles_n;
     float scale;
+    const float *scale_dev;  // device factor on top of scale (nullable)
     int mode;            // GEMM_OUT_F32 or GEMM_OUT_BF16_TERMS
     float *out_f32;
     long long ld_out;    // FP32 output leading dimension
@@ -134,7 +141,7 @@ __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 h) { return *rein
 __device__ __forceinline__ void store_tile_row(const GemmParams &p, const TileJob &j, int row, int col0,
                                                const float (&v)[32]) {
     if (row >= j.out_rows || col0 >= j.out_cols) return;
-    const float s = p.scale;
+    const float s = p.scale_dev ? p.scale * *p.scale_dev : p.scale;
     float x[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) x[c] = (col0 + c < j.valid_cols) ? v[c] * s : 0.0f;
@@ -189,7 +196,7 @@ __device__ __forceinline__ void store_tile_row(const GemmParams &p, const TileJo
     }
 }
 
-template <bool GROUPED>
+template <bool GROUPED, bool FP8>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm_xyT(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, const GemmParams p) {
     extern __shared__ uint8_t smem_raw[];
@@ -250,7 +257,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                         break;
                     }
                     const uint32_t sx = sbase + stage * STAGE_BYTES;
-                    const int kk = kb * BK;
+                    const int kk = kb * (FP8 ? 2 * BK : BK);  // K elements per stage: 128 bytes
                     mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
                     tma_load_2d(sx, &tmX, full_bar(stage), kk % p.kx_period, job.x_row);
                     tma_load_2d(sx + TILE_X_BYTES, &tmY, full_bar(stage), kk, job.y_row);
@@ -270,7 +277,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
-        const uint32_t idesc = idesc_bf16_f32(BM, BN);
+        const uint32_t idesc = FP8 ? idesc_e4m3_f32(BM, BN) : idesc_bf16_f32(BM, BN);
         int stage = 0;
         uint32_t phase = 0;
         int acc = 0;
@@ -296,9 +303,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                     const uint32_t sx = sbase + stage * STAGE_BYTES;
                     const uint32_t sy = sx + TILE_X_BYTES;
 #pragma unroll
-                    for (int k = 0; k < BK / 16; ++k) {
-                        umma_bf16(d_tmem, smem_desc_sw128(sx + 32u * k), smem_desc_sw128(sy + 32u * k), idesc,
-                                  (kb | k) != 0 ? 1u : 0u);
+                    for (int k = 0; k < BK / 16; ++k) {  // 32 bytes of K per instruction
+                        if constexpr (FP8)
+                            umma_f8(d_tmem, smem_desc_sw128(sx + 32u * k), smem_desc_sw128(sy + 32u * k), idesc,
+                                    (kb | k) != 0 ? 1u : 0u);
+                        else
+                            umma_bf16(d_tmem, smem_desc_sw128(sx + 32u * k), smem_desc_sw128(sy + 32u * k), idesc,
+                                      (kb | k) != 0 ? 1u : 0u);
                     }
                     umma_commit(empty_bar(stage));
                 }
@@ -378,18 +389,21 @@ static PFN_encodeTiled_t get_encode_fn() {
     return fn;
 }
 
-// 2-D BF16 tensor map: inner extent `inner` (elements), `rows` rows `stride` elements apart,
-// box 64 x box_rows with the 128-byte swizzle; out-of-range elements read as zero.
+// 2-D tensor map of BF16 (or, fp8, E4M3 bytes): inner extent `inner` (elements), `rows`
+// rows `stride` elements apart, box of 128 bytes x box_rows with the 128-byte swizzle;
+// out-of-range elements read as zero.
 static int make_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows, uint64_t stride,
-                    uint32_t box_rows) {
+                    uint32_t box_rows, bool fp8 = false) {
     PFN_encodeTiled_t enc = get_encode_fn();
     if (!enc) return GOAT_ERR_CUDA;
-    if ((reinterpret_cast<uintptr_t>(base) & 15) || ((stride * 2) & 15)) return GOAT_ERR_INVALID_ARG;
+    const uint64_t es = fp8 ? 1 : 2;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || ((stride * es) & 15)) return GOAT_ERR_INVALID_ARG;
     cuuint64_t dims[2] = {inner, rows};
-    cuuint64_t strides[1] = {stride * 2};
-    cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+    cuuint64_t strides[1] = {stride * es};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / es), box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+    CUresult r = enc(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                     const_cast<void *>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? GOAT_OK : GOAT_ERR_CUDA;
@@ -405,17 +419,21 @@ static int prepare_launch() {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
-        attr_err = cudaFuncSetAttribute(k_gemm_xyT<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        attr_err = cudaFuncSetAttribute(k_gemm_xyT<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)GEMM_SMEM_BYTES);
         if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute(k_gemm_xyT<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            attr_err = cudaFuncSetAttribute(k_gemm_xyT<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)GEMM_SMEM_BYTES);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(k_gemm_xyT<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)GEMM_SMEM_BYTES);
     });
     return (attr_err != cudaSuccess || g_sm_count <= 0) ? GOAT_ERR_CUDA : GOAT_OK;
 }
 
 int gemm_xyT(const GemmCall &c, cudaStream_t stream) {
-    if (c.M < 1 || c.N < 1 || c.k_total < 1 || (c.k_total % BK) || (c.kx_period % BK) || c.kx_period < 1)
+    const int bk = c.fp8 ? 2 * BK : BK;  // K elements per stage
+    if (c.M < 1 || c.N < 1 || c.k_total < 1 || (c.k_total % bk) || (c.kx_period % bk) || c.kx_period < 1)
         return GOAT_ERR_INVALID_ARG;
     {
         const int ps = prepare_launch();
@@ -424,16 +442,17 @@ int gemm_xyT(const GemmCall &c, cudaStream_t stream) {
     const int sm_count = g_sm_count;
 
     CUtensorMap mx, my;
-    int st = make_map(&mx, c.X, (uint64_t)c.kx_period, (uint64_t)c.x_rows, (uint64_t)c.x_stride, BM);
+    int st = make_map(&mx, c.X, (uint64_t)c.kx_period, (uint64_t)c.x_rows, (uint64_t)c.x_stride, BM, c.fp8 != 0);
     if (st) return st;
-    st = make_map(&my, c.Y, (uint64_t)c.k_total, (uint64_t)c.y_rows, (uint64_t)c.y_stride, BN);
+    st = make_map(&my, c.Y, (uint64_t)c.k_total, (uint64_t)c.y_rows, (uint64_t)c.y_stride, BN, c.fp8 != 0);
     if (st) return st;
 
     GemmParams p;
     p.M = c.M;
     p.N = c.N;
     p.kx_period = c.kx_period;
-    p.num_kb = c.k_total / BK;
+    p.num_kb = c.k_total / bk;
+    p.scale_dev = c.scale_dev;
     p.tiles_m = (int)ceil_div(c.M, BM);
     p.tiles_n = (int)ceil_div(c.N, BN);
     p.scale = c.scale;
@@ -449,7 +468,10 @@ int gemm_xyT(const GemmCall &c, cudaStream_t stream) {
     p.err = c.err;
     const int tiles = p.tiles_m * p.tiles_n;
     const int grid = tiles < sm_count ? tiles : sm_count;
-    k_gemm_xyT<false><<<grid, GEMM_THREADS, GEMM_SMEM_BYTES, stream>>>(mx, my, p);
+    if (c.fp8)
+        k_gemm_xyT<false, true><<<grid, GEMM_THREADS, GEMM_SMEM_BYTES, stream>>>(mx, my, p);
+    else
+        k_gemm_xyT<false, false><<<grid, GEMM_THREADS, GEMM_SMEM_BYTES, stream>>>(mx, my, p);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
 }
@@ -475,7 +497,7 @@ int gemm_grouped(const GemmGroupCall &c, cudaStream_t stream) {
     p.num_items = c.num_items;
     p.descs = c.descs;
     const int grid = c.num_items < g_sm_count ? c.num_items : g_sm_count;
-    k_gemm_xyT<true><<<grid, GEMM_THREADS, GEMM_SMEM_BYTES, stream>>>(mx, my, p);
+    k_gemm_xyT<true, false><<<grid, GEMM_THREADS, GEMM_SMEM_BYTES, stream>>>(mx, my, p);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
 }

@@ -16,16 +16,18 @@ enum { GEMM_OUT_F32 = 0, GEMM_OUT_BF16_TERMS = 1 };
 // stride x_stride, read at k mod kx_period; Y: y_rows rows, row stride
 // y_stride, K extent k_total.  Both BF16, 16-byte aligned, K-major.
 struct GemmCall {
-    const __nv_bfloat16 *X;
+    const void *X;           // BF16, or E4M3 bytes when fp8
     int x_rows;
-    long long x_stride;
+    long long x_stride;      // elements
     int kx_period;
-    const __nv_bfloat16 *Y;
+    const void *Y;
     int y_rows;
     long long y_stride;
-    int k_total;
+    int k_total;             // multiple of 64 (BF16) or 128 (E4M3) elements
     int M, N;
+    int fp8;                 // operands E4M3 (kind::f8f6f4), else BF16 (kind::f16)
     float scale;
+    const float *scale_dev;  // device factor on top of scale (nullable)
     int mode;
     float *out_f32;
     long long ld_out;
@@ -99,6 +101,9 @@ struct DevState;
 
 // goat_fw.cu
 int adj_to_bf16(const void *A, int dtype, int n, __nv_bfloat16 *A16, int ld16, float *deg, cudaStream_t s);
+int adj_to_e4m3(const void *A, int dtype, int n, uint8_t *A8, int ld8, cudaStream_t s);
+int bf16_to_e4m3(const __nv_bfloat16 *X, int rows, int ld_src, uint8_t *X8, int ld8, unsigned *amax_bits,
+                 float *inv_scale, cudaStream_t s);
 int count_asym(const void *A, int dtype, int n, int *count_dev, cudaStream_t s);
 void f32_to_terms(const float *X, int n, long long ldx, __nv_bfloat16 *Xb, int ld16, int terms, cudaStream_t s);
 void barycenter(const float *dA, const float *dB, int n, float *G, float *P, DevState *st, cudaStream_t s);

@@ -84,6 +84,17 @@ def test_gradient_bf16_form(n):
     assert err <= 5e-3  # BF16 rounding of P and of Q B: ~1e-3 expected
 
 
+@pytest.mark.parametrize("n", [100, 300, 700])
+def test_gradient_fp8_form(n):
+    # A, B exact in E4M3; Q and Q B rounded to E4M3 (3 mantissa bits) under one
+    # power-of-two scale each: the error budget of the 8-bit form is 2e-2
+    gp = synthetic.rho_er_pair(n, 0.1, 0.8, seed=n)
+    P = random_ds(n, 3).astype(np.float32)
+    G = goat.goat_gradient(cuda(gp.A), cuda(gp.B), cuda(P), precision=goat.GOAT_PREC_FP8)
+    ref = -oracle.gradient(gp.A, gp.B, P.astype(np.float64))
+    assert rel_fro(G.cpu().double().numpy(), ref) <= 2e-2
+
+
 def test_gradient_at_permutation_is_exact_integer():
     # at a permutation every product is an integer sum of 0/1 terms: exact in both forms
     n = 333
@@ -91,7 +102,7 @@ def test_gradient_at_permutation_is_exact_integer():
     P = np.zeros((n, n), np.float32)
     P[np.arange(n), np.random.default_rng(0).permutation(n)] = 1
     ref = -oracle.gradient(gp.A, gp.B, P.astype(np.float64))
-    for prec in (goat.GOAT_PREC_BF16, goat.GOAT_PREC_FP32):
+    for prec in (goat.GOAT_PREC_BF16, goat.GOAT_PREC_FP32, goat.GOAT_PREC_FP8):
         G = goat.goat_gradient(cuda(gp.A), cuda(gp.B), cuda(P), precision=prec)
         np.testing.assert_array_equal(G.cpu().double().numpy(), ref)
 
@@ -340,7 +351,7 @@ def test_match_isomorphic_recovery():
         assert obj == gp.A.sum()
 
 
-@pytest.mark.parametrize("precision,warm", [(1, 0), (0, 1)])
+@pytest.mark.parametrize("precision,warm", [(1, 0), (0, 1), (2, 1)])
 def test_match_accuracy_within_one_point_of_oracle(precision, warm):
     # 20 seeds of the n = 100, p = 0.1, rho = 0.9 workload: mean matching accuracy
     # and disagreements within 1 percentage point of the FP64 oracle's
