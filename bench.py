@@ -147,12 +147,12 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
-def gemm_traffic_per_launch(n: int):
-    """DRAM bytes per GEMM launch from the committed ncu summary, scaled to n, or None.
+def gemm_traffic_per_launch(n: int, name: str = "k_gemm_xyT_traffic.txt"):
+    """DRAM bytes per GEMM launch from the committed ncu summary `name`, scaled to n, or None.
 
     The summary records the kernel source hash it was taken with; a changed
     kernel invalidates it."""
-    path = os.path.join(ROOT, "profiles", "k_gemm_xyT_traffic.txt")
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     kv = {}
@@ -501,7 +501,7 @@ def main():
         peak = 2.0 * peaks["bf16_tflops_sustained"]
         kernel = "k_gemm_xyT (E4M3 kind::f8f6f4, one n x n x n product per launch)"
         peak_source = f"{peaks['source']} bf16_tflops_sustained x nominal fp8/bf16 ratio 2"
-        traffic = None  # the committed DRAM capture is of the BF16 instantiation
+        traffic = gemm_traffic_per_launch(n, "k_gemm_xyT_fp8_traffic.txt")
     else:
         peak = peaks["bf16_tflops_sustained"]
         kernel = "k_gemm_xyT (BF16 kind::f16, one n x n x n product per launch)"
