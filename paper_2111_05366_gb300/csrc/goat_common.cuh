@@ -41,6 +41,8 @@ struct DevState {
     int lap_changed;      // price relaxation: any price raised this round
     int lap_phase_done;
     int lap_free;         // shortest-augmenting-path step: rows it has to place
+    int lap_nb[2];        // Jacobi bidder list lengths (alternate rounds)
+    int pad1;
     int asym_count;
     int bad_perm;
     double lap_eps;

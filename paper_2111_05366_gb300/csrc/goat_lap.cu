@@ -62,6 +62,7 @@ struct SapSlot {
 struct LapBuffers {
     i64 *price, *my_bid;
     int *owner, *assign, *my_obj, *bwin, *queue;
+    int *blist[2];    // rows bidding in alternate Jacobi rounds
     unsigned long long *bbest;
     int *sap_pred;    // predecessor row of every column after a search
     int *tflag, *tlist, *mark_row, *mark_col;  // augmenting-path targets and the vertices used
@@ -78,7 +79,7 @@ size_t lap_bytes(int n, int /*nchunks*/) {
     return 2 * (size_t)n * sizeof(i64) + 5 * (size_t)n * sizeof(int) + (size_t)n * 8 + 16 * 256 +
            (size_t)n * sizeof(int) + 2 * (size_t)n * (sizeof(int) + sizeof(i64)) + 4 * sizeof(SapSlot) + 6 * 256 +
            4 * (size_t)n * sizeof(int) + 2 * (size_t)n * sizeof(i64) + 6 * 256 +
-           2 * (size_t)n * (sizeof(int) + sizeof(i64)) + 4 * 256;
+           2 * (size_t)n * (sizeof(int) + sizeof(i64)) + 4 * 256 + 2 * (size_t)n * sizeof(int) + 2 * 256;
 }
 
 static LapBuffers carve(void *base, int n) {
@@ -106,6 +107,8 @@ static LapBuffers carve(void *base, int n) {
     L.fj0[1] = (int *)take(sizeof(int) * n);
     L.fdl[0] = (i64 *)take(sizeof(i64) * n);
     L.fdl[1] = (i64 *)take(sizeof(i64) * n);
+    L.blist[0] = (int *)take(sizeof(int) * n);
+    L.blist[1] = (int *)take(sizeof(int) * n);
     L.ring = (SapSlot *)take(4 * sizeof(SapSlot));
     L.tflag = (int *)take(sizeof(int) * n);
     L.tlist = (int *)take(sizeof(int) * n);
@@ -203,26 +206,42 @@ __global__ void k_lap_reset(int n, const LapBuffers L, DevState *st, int reset_p
         L.bwin[j] = INT_MAX;
         L.my_obj[j] = -1;
         if (reset_prices) L.price[j] = 0;
+        L.blist[0][j] = j;  // every row bids in the first round of a phase
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->lap_unassigned = n;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->lap_unassigned = n;
+        st->lap_nb[0] = n;
+    }
 }
 
-// Jacobi bidding: one CTA per unassigned row (a row of 4n bytes is too long for
-// one warp to stream at speed once few rows are left bidding).
-__global__ void __launch_bounds__(256) k_lap_bid(const float *__restrict__ M, int n, const Quant q,
-                                                 const LapBuffers L, i64 eps, const DevState *st) {
-    if (st->lap_unassigned == 0) return;
-    __shared__ i64 s_b1[8], s_b2[8];
-    __shared__ int s_j1[8];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    for (int i = blockIdx.x; i < n; i += gridDim.x) {
-        if (L.assign[i] >= 0) {  // block-uniform: assign[] does not change during the kernel
-            if (tid == 0) L.my_obj[i] = -1;
-            continue;
-        }
+// Appends the rows of the `want` lanes to a bidder list (one atomic per warp).
+__device__ __forceinline__ void list_append(bool want, int row, int *dst, int *count) {
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, first = __ffs(m) - 1;
+    int base = 0;
+    if (lane == first) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, first);
+    if (want) dst[base + __popc(m & ((1u << lane) - 1u))] = row;
+}
+
+// Jacobi bidding over the rows listed for this round (blist[cur], lap_nb[cur]
+// entries): one CTA per bidding row (a row of 4n bytes is too long for one warp
+// to stream at speed); the next round's list starts empty.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_lap_bid(const float *__restrict__ M, int n, const Quant q,
+                                                     const LapBuffers L, i64 eps, DevState *st, int cur) {
+    const int cnt = st->lap_nb[cur];
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->lap_nb[cur ^ 1] = 0;
+    constexpr int NW = THREADS / 32;
+    __shared__ i64 s_b1[NW], s_b2[NW];
+    __shared__ int s_j1[NW];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
+        const int i = L.blist[cur][idx];
         i64 b1 = kNegInf, b2 = kNegInf;
         int j1 = INT_MAX;
-        top2_scan(M + (long long)i * n, L.price, n, q, tid, blockDim.x, i, b1, b2, j1);
+        top2_scan(M + (long long)i * n, L.price, n, q, tid, THREADS, i, b1, b2, j1);
         top2_warp(b1, b2, j1);
         if (lane == 0) {
             s_b1[warp] = b1;
@@ -231,7 +250,7 @@ __global__ void __launch_bounds__(256) k_lap_bid(const float *__restrict__ M, in
         }
         __syncthreads();
         if (tid == 0) {
-            for (int w = 1; w < nwarps; ++w) top2_merge(b1, b2, j1, s_b1[w], s_b2[w], s_j1[w]);
+            for (int w = 1; w < NW; ++w) top2_merge(b1, b2, j1, s_b1[w], s_b2[w], s_j1[w]);
             j1 = tie_key_to_col(j1, i, n);
             const i64 inc = (b2 == kNegInf) ? eps : (b1 - b2) + eps;
             const i64 bid = L.price[j1] + inc;
@@ -243,29 +262,48 @@ __global__ void __launch_bounds__(256) k_lap_bid(const float *__restrict__ M, in
     }
 }
 
-__global__ void k_lap_win(int n, const LapBuffers L, const DevState *st) {
-    if (st->lap_unassigned == 0) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+// Each object's winner: the highest bid, the lowest row among equal ones.
+__global__ void k_lap_win(const LapBuffers L, const DevState *st, int cur) {
+    const int cnt = st->lap_nb[cur];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+        const int i = L.blist[cur][k];
         const int j = L.my_obj[i];
-        if (j >= 0 && L.bbest[j] == (unsigned long long)L.my_bid[i]) atomicMin(&L.bwin[j], i);
+        if (L.bbest[j] == (unsigned long long)L.my_bid[i]) atomicMin(&L.bwin[j], i);
     }
 }
 
-__global__ void k_lap_assign(int n, const LapBuffers L, DevState *st) {
-    if (st->lap_unassigned == 0) return;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const int w = L.bwin[j];
-        if (w == INT_MAX) continue;
-        const int old = L.owner[j];
-        if (old >= 0)
-            L.assign[old] = -1;
-        else
-            atomicSub(&st->lap_unassigned, 1);
-        L.owner[j] = w;
-        L.assign[w] = j;
-        L.price[j] = (i64)L.bbest[j];
-        L.bbest[j] = 0ull;
-        L.bwin[j] = INT_MAX;
+// Winners take their objects at their bids and evict the previous holders; the
+// evicted rows and the outbid bidders make up the next round's list.  (An outbid
+// row reads bwin[j] while the winner may be resetting it: either value differs
+// from the outbid row, so the outcome is the same.)
+__global__ void k_lap_assign(const LapBuffers L, DevState *st, int cur) {
+    const int cnt = st->lap_nb[cur];
+    int *next = L.blist[cur ^ 1];
+    int *ncount = &st->lap_nb[cur ^ 1];
+    const int stride = gridDim.x * blockDim.x;
+    const int rounds = (cnt + stride - 1) / stride;  // uniform trip count for the warp ballots
+    for (int r = 0; r < rounds; ++r) {
+        const int k = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        int push = -1;
+        if (k < cnt) {
+            const int i = L.blist[cur][k];
+            const int j = L.my_obj[i];
+            if (L.bwin[j] == i) {
+                const int old = L.owner[j];
+                if (old >= 0) {
+                    L.assign[old] = -1;
+                    push = old;
+                }
+                L.owner[j] = i;
+                L.assign[i] = j;
+                L.price[j] = (i64)L.bbest[j];
+                L.bbest[j] = 0ull;
+                L.bwin[j] = INT_MAX;
+            } else {
+                push = i;
+            }
+        }
+        list_append(push >= 0, push, next, ncount);
     }
 }
 
@@ -1193,19 +1231,27 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
         note_launches(1);
         int left = n;
         auto t0 = clk::now();
+        int cur = 0;  // the list the next round bids from
         for (int hr = 0; hr < ctl.head_rounds && rounds < ctl.max_rounds; hr += 4) {
+            // many bidders: many CTAs of 256 threads; few: one 1024-thread CTA per row
+            const bool light = left <= sms;
+            const int gb = light ? std::max(1, left) : growb;
             for (int b = 0; b < 4; ++b) {
-                k_lap_bid<<<growb, 256, 0, s>>>(M, n, q, L, eps, st);
-                note_launches(1);
-                k_lap_win<<<g1, 256, 0, s>>>(n, L, st);
-                note_launches(1);
-                k_lap_assign<<<g1, 256, 0, s>>>(n, L, st);
-                note_launches(1);
+                if (light)
+                    k_lap_bid<1024><<<gb, 1024, 0, s>>>(M, n, q, L, eps, st, cur);
+                else
+                    k_lap_bid<256><<<gb, 256, 0, s>>>(M, n, q, L, eps, st, cur);
+                k_lap_win<<<g1, 256, 0, s>>>(L, st, cur);
+                k_lap_assign<<<g1, 256, 0, s>>>(L, st, cur);
+                note_launches(3);
+                cur ^= 1;
             }
             rounds += 4;
-            left = poll_int(&st->lap_unassigned, host_pinned, s);
+            left = poll_int(&st->lap_nb[cur], host_pinned, s);
             if (left <= head_threshold) break;
         }
+        // the tail and the searches find the free rows from assign[]
+        cudaMemcpyAsync(&st->lap_unassigned, &st->lap_nb[cur], sizeof(int), cudaMemcpyDeviceToDevice, s);
         R.ms_head += ms_since(t0);
         const long long budget = ctl.tail_bids >= 0 ? ctl.tail_bids
                                  : last             ? std::max(4LL * n, 262144LL)
