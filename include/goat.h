@@ -232,11 +232,11 @@ GOAT_API int goat_project(const float *M, int n, int maximize, int32_t *perm_out
 typedef struct goat_lap_options {
     int max_rounds;       /* parallel (Jacobi) bidding rounds over all phases, default 1<<20   */
     int head_rounds;      /* Jacobi rounds per eps phase before the sequential steps (the rounds
-                             stop early once at most 16 rows bid), default 256                */
+                             stop early once at most 4 rows bid), default 256                 */
     long long tail_bids;  /* sequential (Gauss-Seidel) bids per phase, default max(n, 65536),
                              max(4n, 262144) in the last phase; 0 skips that step            */
     long long tail_stall; /* bids in a row that do not shorten the queue of unassigned rows
-                             and end the sequential bidding, default max(512, n / 32)         */
+                             and end the sequential bidding, default max(128, n / 256)        */
     long long sap_pops;   /* row scans the shortest-augmenting-path searches may do per phase,
                              default 8n + 2^16 (64n + 2^20 in the last phase); 0 disables them */
 } goat_lap_options;

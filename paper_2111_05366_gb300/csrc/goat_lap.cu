@@ -1197,7 +1197,7 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
     i64 eps = std::max<i64>(1, c_int / 4);
     int rounds = 0;
     bool exhausted = false;
-    const int head_threshold = 16;
+    const int head_threshold = 4;
     // the cluster kernels hold per-column state of n / 8 columns in each CTA's shared memory
     const int cw = (n + LAP_CLUSTER - 1) / LAP_CLUSTER;
     const size_t tail_smem = (size_t)cw * (sizeof(i64) + sizeof(int));
@@ -1223,7 +1223,7 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
         if (sap_cpt) sap_grid = (int)std::max<int64_t>(1, ceil_div(n, (int64_t)SAP_SLOTS * sap_cpt));
     }
     const bool use_sap = sap_cpt > 0;
-    const long long stall = ctl.tail_stall >= 0 ? ctl.tail_stall : std::max(512LL, (long long)n / 32);
+    const long long stall = ctl.tail_stall >= 0 ? ctl.tail_stall : std::max(128LL, (long long)n / 256);
     for (;;) {
         const bool last = eps <= 1;
         ++R.phases;
