@@ -126,7 +126,7 @@ def _cost(n, seed):
     return (-oracle.gradient(gp.A, gp.B, P)).astype(np.float32)
 
 
-@pytest.mark.parametrize("n,iters", [(100, 5), (300, 20), (517, 50)])
+@pytest.mark.parametrize("n,iters", [(100, 5), (300, 20), (517, 50), (1024, 20), (4100, 8)])
 def test_sinkhorn_fixed_iterations_match_oracle(n, iters):
     G = _cost(n, n)
     eps = 0.03 * float(np.abs(G).max())
@@ -153,6 +153,18 @@ def test_sinkhorn_converges_to_tolerance(n):
     # same fixed point as the oracle (Sinkhorn's limit is unique)
     Qo, *_ = oracle.lot(G.astype(np.float64), eps, 1e-10, 100000)
     np.testing.assert_allclose(Qh, Qo, atol=5e-4)
+
+
+def test_sinkhorn_converges_to_tolerance_n2048():
+    # a larger case: marginals within the tolerance from a cold start
+    n = 2048
+    G = _cost(n, 11)
+    eps = 0.03 * float(np.abs(G).max())
+    f, g, Q, it, resid = goat.goat_sinkhorn(cuda(G), eps, 1e-5, 5000, want_Q=True)
+    assert resid < 1e-5 and it < 5000
+    Qh = Q.cpu().double().numpy()
+    assert np.abs(Qh.sum(0) - 1).max() < 1e-4
+    assert np.abs(Qh.sum(1) - 1).max() < 1e-4
 
 
 def test_sinkhorn_separable_cost_gives_barycenter():
