@@ -392,6 +392,43 @@ def run_batched_case(args):
 
 # ------------------------------------------------------------------ our arm
 
+class Ranks:
+    """Barrier and reductions over the ranks of a weak-scaling run (replicas: one
+    independent pair per rank; the only communication is the timing reduction)."""
+
+    def __init__(self, world: int, device: str):
+        self.world = world
+        self.device = device
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def _reduce(self, x: float, op) -> float:
+        if self.world == 1:
+            return x
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x: float) -> float:
+        import torch.distributed as dist
+        return self._reduce(x, dist.ReduceOp.MAX)
+
+    def sum(self, x: float) -> float:
+        import torch.distributed as dist
+        return self._reduce(x, dist.ReduceOp.SUM)
+
+
+def whole_job_rate(ranks: Ranks, units: float, ms: float) -> float:
+    """Units all ranks processed / the slowest rank's time (the timed region is
+    bracketed by barriers, so the slowest rank spans the job)."""
+    return ranks.sum(units) / (ranks.max(ms) / 1000.0)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -412,23 +449,8 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    ranks = Ranks(world, "cuda")
+    barrier, max_over_ranks, sum_over_ranks = ranks.barrier, ranks.max, ranks.sum
 
     goat.load()
     n = args.n
@@ -479,8 +501,7 @@ def main():
     log(f"chosen form timed: {ms:.0f} ms for {args.steps} solves")
     fw_iters = sum(o[2]["fw_iters"] for o in outs)
     ms_max = max_over_ranks(ms)
-    iters_all = sum_over_ranks(float(fw_iters))
-    value = iters_all / (ms_max / 1000.0)
+    value = whole_job_rate(ranks, float(fw_iters), ms)
     st = outs[-1][2]
     acc = float((outs[-1][0] == gp.truth).mean())
 
