@@ -143,6 +143,7 @@ struct LapControl {
     long long tail_bids;   // Gauss-Seidel bids per phase
     long long tail_stall;  // bids without the queue shrinking that end the Gauss-Seidel tail
     long long sap_pops;    // row scans the augmenting-path searches may do per phase (0: none)
+    int sap_step;          // columns a search settles per parallel step
 };
 void lap_default_control(LapControl *c);
 struct LapReport {

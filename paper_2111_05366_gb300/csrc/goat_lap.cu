@@ -605,7 +605,7 @@ constexpr int SAP_SLOTS = 256;                  // column slots per CTA (each CP
 constexpr int SAP_GROUPS = 2;                   // row groups sharing the slots in a relaxation
 constexpr int SAP_THREADS = SAP_SLOTS * SAP_GROUPS;
 constexpr int SAP_STAGE = 512;                  // frontier entries staged in shared memory at a time
-constexpr int SAP_STEP = 256;                   // open columns settled per parallel step (more on exact ties)
+constexpr int SAP_STEP = 128;                   // default: open columns settled per parallel step (more on ties)
 constexpr i64 kPosInf = LLONG_MAX / 4;
 
 // Reduced cost of (i, j) in the minimisation form: c~_ij = -a~_ij, the benefit of
@@ -642,7 +642,7 @@ __device__ __forceinline__ void block_min2(i64 &x, i64 &y, i64 *sx, i64 *sy) {
 // Hungarian method in Jonker-Volgenant's form: each search starts from all free
 // rows at once (row potentials u_i = min_j (c~_ij - v_j) from the prep kernel;
 // they stay feasible since the duals v only fall) and runs a label-correcting
-// Dijkstra that settles up to SAP_STEP columns per parallel step: the open columns
+// Dijkstra that settles up to step_cols columns per parallel step: the open columns
 // (free columns aside) with the least labels, chosen by a histogram of the labels
 // gathered in the previous step.  Their rows are scanned in parallel (each thread
 // relaxes its columns over the listed rows); a settled column whose label still
@@ -657,7 +657,7 @@ __device__ __forceinline__ void block_min2(i64 &x, i64 &y, i64 *sx, i64 *sy) {
 // over stay unassigned (lap_unassigned reports them).
 template <int CPT>
 __global__ void __launch_bounds__(SAP_THREADS) k_lap_sap_grid(const float *__restrict__ M, int n, const Quant q,
-                                                              const LapBuffers L, i64 delta0, long long max_scans,
+                                                              const LapBuffers L, int step_cols, long long max_scans,
                                                               DevState *st) {
     namespace cg = cooperative_groups;
     cg::grid_group grid = cg::this_grid();
@@ -761,7 +761,7 @@ __global__ void __launch_bounds__(SAP_THREADS) k_lap_sap_grid(const float *__res
         }
         if (tid < 64 && s_hist[tid]) atomicAdd(&cur().hist[tid], s_hist[tid]);
     };
-    // the widest bound tau = base + 2^b - 1 taking in at most SAP_STEP open non-free
+    // the widest bound tau = base + 2^b - 1 taking in at most step_cols open non-free
     // columns (never none), capped below the least free label; nbase = the lower edge
     // of the lowest non-empty histogram bin, a lower bound of every label from now on
     auto choose_tau = [&](i64 base, i64 tmin, i64 *tau, i64 *nbase) {
@@ -773,7 +773,7 @@ __global__ void __launch_bounds__(SAP_THREADS) k_lap_sap_grid(const float *__res
             for (int b = 0; b < 64; ++b) {
                 cum += h[b];
                 if (h[b] && first < 0) first = b;
-                if (cum <= SAP_STEP) best = b;
+                if (cum <= step_cols) best = b;
             }
             if (first < 0) first = 0;
             if (best < first) best = first;
@@ -1152,6 +1152,7 @@ void lap_default_control(LapControl *c) {
     c->tail_bids = -1;
     c->tail_stall = -1;
     c->sap_pops = -1;
+    c->sap_step = -1;
 }
 
 // Runs the projection.  lap_ws must hold lap_bytes(n, ...) bytes; cost_dev
@@ -1276,12 +1277,12 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
             cudaMemsetAsync(L.mark_row, 0, sizeof(int) * n, s);
             cudaMemsetAsync(L.mark_col, 0, sizeof(int) * n, s);
             k_lap_sap_prep<<<growb, 256, 0, s>>>(M, n, q, L, st);
-            i64 delta0 = std::max<i64>(1, eps);
+            int step_cols = ctl.sap_step > 0 ? ctl.sap_step : SAP_STEP;
             long long max_scans = pops;
             DevState *stp = st;
             const float *Mp = M;
             int nn = n;
-            void *args[] = {(void *)&Mp, (void *)&nn, (void *)&q, (void *)&L, (void *)&delta0, (void *)&max_scans,
+            void *args[] = {(void *)&Mp, (void *)&nn, (void *)&q, (void *)&L, (void *)&step_cols, (void *)&max_scans,
                             (void *)&stp};
             const void *fn = sap_cpt == 1   ? (const void *)k_lap_sap_grid<1>
                              : sap_cpt == 2 ? (const void *)k_lap_sap_grid<2>
