@@ -54,3 +54,26 @@ def test_binding_names_match_abi():
     for name in ["goat_match", "goat_match_host", "goat_gradient", "goat_sinkhorn", "goat_line_search",
                  "goat_fw_update", "goat_project", "goat_objective"]:
         assert callable(getattr(goat, name))
+
+
+def test_projection_schedule_defaults(lib_path):
+    import paper_2111_05366_gb300 as goat
+    o = goat.lap_options()
+    assert o.max_rounds == 1 << 20 and o.head_rounds == 256
+    assert o.tail_bids == -1 and o.tail_stall == -1 and o.sap_pops == -1
+    o = goat.lap_options(tail_bids=0, sap_pops=7)
+    assert o.tail_bids == 0 and o.sap_pops == 7
+
+
+def test_workspace_sizes_grow_with_the_form(lib_path):
+    # host arithmetic only: the FP32 form doubles the operand buffers, the 8-bit
+    # form adds four n x round_up(n, 128) byte operands
+    import paper_2111_05366_gb300 as goat
+    for n in (100, 1000, 4097):
+        b16 = goat.workspace_bytes(n, goat.GOAT_DTYPE_U8, goat.GOAT_PREC_BF16)
+        f32 = goat.workspace_bytes(n, goat.GOAT_DTYPE_U8, goat.GOAT_PREC_FP32)
+        f8 = goat.workspace_bytes(n, goat.GOAT_DTYPE_U8, goat.GOAT_PREC_FP8)
+        ld, ld8 = -(-n // 64) * 64, -(-n // 128) * 128
+        assert f32 - b16 >= 2 * n * ld * 2 - 1024  # Xq and C1 gain a second BF16 term (256-byte rounding)
+        assert f8 - b16 >= 4 * n * ld8 - 1024      # A8, B8, Q8, C8
+        assert goat.workspace_bytes(n, goat.GOAT_DTYPE_U8, goat.GOAT_PREC_BF16, host=True) > b16
