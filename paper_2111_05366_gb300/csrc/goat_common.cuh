@@ -246,7 +246,6 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor for kind::f16: BF16 x BF16 -> FP32, both operands K-major.
 // kind::f8f6f4 instruction descriptor: A and B E4M3 (format code 0), D F32, K-major both.
 __host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N) {
     return (1u << 4)                       // D format: F32
@@ -256,6 +255,7 @@ __host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N) {
            | ((uint32_t)(M >> 4) << 24);   // M / 16
 }
 
+// Instruction descriptor for kind::f16: BF16 x BF16 -> FP32, both operands K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4)                       // D format: F32
            | (1u << 7)                     // A format: BF16

@@ -55,19 +55,32 @@ __global__ void __launch_bounds__(256) k_adj_to_e4m3(const T *__restrict__ A, in
     }
 }
 
-// max |x| of a BF16 matrix (non-negative float bits, atomicMax).
+// max |x| of a BF16 matrix (non-negative float bits, atomicMax); total is a
+// multiple of 8 and X 16-byte aligned (operand buffers), read 16 bytes at a time.
 __global__ void __launch_bounds__(256) k_absmax_bf16(const __nv_bfloat16 *__restrict__ X, long long total,
                                                      unsigned *out) {
     float m = 0.0f;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x)
-        m = fmaxf(m, fabsf(__bfloat162float(X[t])));
+    const uint4 *X8 = reinterpret_cast<const uint4 *>(X);
+    const long long total8 = total >> 3;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total8;
+         t += (long long)gridDim.x * blockDim.x) {
+        const uint4 v = __ldg(X8 + t);
+        const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            // |x| of a BF16 is its bits without the sign; as the upper half of a float it orders the same
+            m = fmaxf(m, __uint_as_float((w[k] & 0x7FFFu) << 16));
+            m = fmaxf(m, __uint_as_float(w[k] & 0x7FFF0000u));
+        }
+    }
     m = warp_max(m);
     if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(out, __float_as_uint(m));
 }
 
 // BF16 matrix (rows x ld_src) -> E4M3 (rows x ld8, zero padding) scaled by s, the
-// largest power of two with s max|x| <= 448; inv_scale <- 1 / s (exact).
+// largest power of two with s max|x| <= 448; inv_scale <- 1 / s (exact).  One
+// thread per 16 output bytes; ld_src is a multiple of 64 and ld8 of 128, so a
+// 16-column chunk lies wholly inside the source row or wholly in the padding.
 __global__ void __launch_bounds__(256) k_bf16_to_e4m3(const __nv_bfloat16 *__restrict__ X, int rows, int ld_src,
                                                       uint8_t *__restrict__ X8, int ld8, const unsigned *amax_bits,
                                                       float *inv_scale) {
@@ -76,15 +89,23 @@ __global__ void __launch_bounds__(256) k_bf16_to_e4m3(const __nv_bfloat16 *__res
     const float q = amax > 0.0f ? 448.0f / amax : 1.0f;
     const float sc = __uint_as_float(__float_as_uint(q) & 0x7F800000u);
     if (blockIdx.x == 0 && threadIdx.x == 0) *inv_scale = 1.0f / sc;
-    const int pairs = ld8 / 2;
-    const long long total = (long long)rows * pairs;
+    const int cpr = ld8 / 16;  // 16-column chunks per row
+    const long long total = (long long)rows * cpr;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t / pairs), j = (int)(t - (long long)i * pairs) * 2;
-        const __nv_bfloat16 *src = X + (long long)i * ld_src;
-        const float a = j < ld_src ? __bfloat162float(src[j]) * sc : 0.0f;
-        const float b = j + 1 < ld_src ? __bfloat162float(src[j + 1]) * sc : 0.0f;
-        *reinterpret_cast<unsigned short *>(X8 + (long long)i * ld8 + j) = e4m3x2(a, b);
+        const int i = (int)(t / cpr), j = (int)(t - (long long)i * cpr) * 16;
+        uint4 out = make_uint4(0u, 0u, 0u, 0u);
+        if (j < ld_src) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(X + (long long)i * ld_src + j);
+            const uint4 v0 = __ldg(src), v1 = __ldg(src + 1);
+            const unsigned w[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+            unsigned b[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                b[k] = e4m3x2(__uint_as_float(w[k] << 16) * sc, __uint_as_float(w[k] & 0xFFFF0000u) * sc);
+            out = make_uint4(b[0] | (b[1] << 16), b[2] | (b[3] << 16), b[4] | (b[5] << 16), b[6] | (b[7] << 16));
+        }
+        *reinterpret_cast<uint4 *>(X8 + (long long)i * ld8 + j) = out;
     }
 }
 
@@ -481,9 +502,9 @@ int bf16_to_e4m3(const __nv_bfloat16 *X, int rows, int ld_src, uint8_t *X8, int 
                  float *inv_scale, cudaStream_t s) {
     note_launches(2);
     cudaMemsetAsync(amax_bits, 0, sizeof(unsigned), s);
-    k_absmax_bf16<<<grid_for((long long)rows * ld_src), 256, 0, s>>>(X, (long long)rows * ld_src, amax_bits);
-    k_bf16_to_e4m3<<<grid_for((long long)rows * (ld8 / 2)), 256, 0, s>>>(X, rows, ld_src, X8, ld8, amax_bits,
-                                                                         inv_scale);
+    k_absmax_bf16<<<grid_for((long long)rows * ld_src / 8), 256, 0, s>>>(X, (long long)rows * ld_src, amax_bits);
+    k_bf16_to_e4m3<<<grid_for((long long)rows * (ld8 / 16)), 256, 0, s>>>(X, rows, ld_src, X8, ld8, amax_bits,
+                                                                          inv_scale);
     return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
 }
 

@@ -143,12 +143,12 @@ constexpr i64 kNegInf = LLONG_MIN / 4;
 __device__ __forceinline__ int col_to_tie_key(int j, int i, int n) { return j >= i ? j - i : j - i + n; }
 __device__ __forceinline__ int tie_key_to_col(int k, int i, int n) { return k + i < n ? k + i : k + i - n; }
 
-// Top-2 of v_j = a_ij - p_j over j = first, first + stride, ... < n, 8 loads in
+// Top-2 of v_j = a_ij - p_j over j = first, first + stride, ... < n, U loads in
 // flight; j1 is the tie key of the best object of bidder `row`.
+template <int U = 8>
 __device__ __forceinline__ void top2_scan(const float *__restrict__ Mi, const i64 *__restrict__ price, int n,
                                           const Quant q, int first, int stride, int row, i64 &b1, i64 &b2,
                                           int &j1) {
-    constexpr int U = 8;
     for (int base = first; base < n; base += U * stride) {
         float m[U];
         i64 pr[U];
