@@ -38,15 +38,10 @@ struct DevState {
     int error;            // first device-side error (goat_status), 0 if none
     double ls_a, ls_b, ls_dd, alpha;
     int lap_unassigned;   // auction: bidders without an object
-    int lap_changed;      // price relaxation: any price raised this round
-    int lap_phase_done;
     int lap_free;         // shortest-augmenting-path step: rows it has to place
     int lap_nb[2];        // Jacobi bidder list lengths (alternate rounds)
-    int pad1;
     int asym_count;
     int bad_perm;
-    double lap_eps;
-    double lap_gap;
     long long lap_bids;   // Gauss-Seidel bids of the projection so far
     long long lap_pops;   // rows scanned by its shortest-augmenting-path searches
     long long lap_epochs; // grid-wide steps of those searches

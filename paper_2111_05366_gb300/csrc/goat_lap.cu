@@ -52,10 +52,10 @@ typedef long long i64;
 
 // Grid-wide reduction slot of the augmenting-path searches (one per barrier epoch).
 struct SapSlot {
-    long long minv;  // least label of the open columns
-    long long tmin;  // least label of the free columns in the bucket
+    long long minv;  // least label of the open non-free columns
+    long long tmin;  // least label of the free columns
     int count;       // rows appended to the epoch's frontier list
-    int tj;          // lowest free bucket column with label tmin
+    int pad;
     int hist[64];    // open non-free columns by bit length of (label - base)
 };
 
@@ -699,7 +699,6 @@ __global__ void __launch_bounds__(SAP_THREADS) k_lap_sap_grid(const float *__res
             L.ring[k].minv = kPosInf;
             L.ring[k].tmin = kPosInf;
             L.ring[k].count = 0;
-            L.ring[k].tj = INT_MAX;
         }
     if (blockIdx.x == 0 && tid < 64)
         for (int k = 0; k < 4; ++k) L.ring[k].hist[tid] = 0;
@@ -711,7 +710,6 @@ __global__ void __launch_bounds__(SAP_THREADS) k_lap_sap_grid(const float *__res
             z.minv = kPosInf;
             z.tmin = kPosInf;
             z.count = 0;
-            z.tj = INT_MAX;
         }
         if (blockIdx.x == 0 && tid < 64) z.hist[tid] = 0;
     };

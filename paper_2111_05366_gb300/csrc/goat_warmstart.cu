@@ -76,25 +76,43 @@ __global__ void __launch_bounds__(256) k_feat_rows(const float *__restrict__ G, 
     }
 }
 
-// Column statistics of G (one thread per column; rows in order).
+// Column statistics of G: a CTA takes 32 columns (one 128-byte segment per row)
+// and 8 row groups; each thread runs over rows g, g + 8, ... and the groups are
+// merged in shared memory in a fixed order.
 __global__ void __launch_bounds__(256) k_feat_cols(const float *__restrict__ G, int n, float inv_eps,
                                                    float *__restrict__ stats) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
+    __shared__ float sh[4][8][33];
+    const int c = threadIdx.x & 31, rg = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + c;
     float s = 0.f, s2 = 0.f, mx = -INFINITY, mn = INFINITY;
-    for (int i = 0; i < n; ++i) {
-        const float x = G[(long long)i * n + j] * inv_eps;
-        s += x;
-        s2 += x * x;
-        mx = fmaxf(mx, x);
-        mn = fminf(mn, x);
+    if (j < n) {
+        for (int i = rg; i < n; i += 8) {
+            const float x = G[(long long)i * n + j] * inv_eps;
+            s += x;
+            s2 += x * x;
+            mx = fmaxf(mx, x);
+            mn = fminf(mn, x);
+        }
     }
-    const float mean = s / n;
-    float *o = stats + (long long)(n + j) * 4;
-    o[0] = mean;
-    o[1] = mx;
-    o[2] = sqrtf(fmaxf(s2 / n - mean * mean, 0.f));
-    o[3] = mn;
+    sh[0][rg][c] = s;
+    sh[1][rg][c] = s2;
+    sh[2][rg][c] = mx;
+    sh[3][rg][c] = mn;
+    __syncthreads();
+    if (rg == 0 && j < n) {
+        for (int g = 1; g < 8; ++g) {
+            s += sh[0][g][c];
+            s2 += sh[1][g][c];
+            mx = fmaxf(mx, sh[2][g][c]);
+            mn = fminf(mn, sh[3][g][c]);
+        }
+        const float mean = s / n;
+        float *o = stats + (long long)(n + j) * 4;
+        o[0] = mean;
+        o[1] = mx;
+        o[2] = sqrtf(fmaxf(s2 / n - mean * mean, 0.f));
+        o[3] = mn;
+    }
 }
 
 // 2-hop degrees (A d_A)_i and (B d_B)_j (one warp per row).
@@ -269,7 +287,7 @@ int dual_features(const float *G, const void *A, const void *B, int n, int dtype
         k_feat_rows<float><<<gw, 256, 0, s>>>(G, (const float *)A, (const float *)B, n, inv_eps, stats, deg, sums);
         k_feat_hop2<float><<<gw, 256, 0, s>>>((const float *)A, (const float *)B, n, deg, hop2, sums);
     }
-    k_feat_cols<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(G, n, inv_eps, stats);
+    k_feat_cols<<<(unsigned)ceil_div(n, 32), 256, 0, s>>>(G, n, inv_eps, stats);
     k_feat_assemble<<<(unsigned)ceil_div(2LL * n, 256), 256, 0, s>>>(n, stats, deg, hop2, sums, feats);
     note_launches(4);
     return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
