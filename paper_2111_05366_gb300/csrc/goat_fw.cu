@@ -202,6 +202,39 @@ __device__ __forceinline__ float q_terms(const __nv_bfloat16 *row, int ldq, int 
     return q;
 }
 
+// Four columns of one row for the line-search sums: G, G_Q, P and Q (BF16 terms).
+struct LsQuad {
+    float4 g, h, p;
+    float q[4];
+};
+
+__device__ __forceinline__ LsQuad ls_load(const float *__restrict__ G, const float *__restrict__ GQ,
+                                          const float *__restrict__ P, const __nv_bfloat16 *__restrict__ qrow, int ldq,
+                                          int terms, long long base, int j) {
+    LsQuad u;
+    u.g = *reinterpret_cast<const float4 *>(G + base + j);
+    u.h = *reinterpret_cast<const float4 *>(GQ + base + j);
+    u.p = *reinterpret_cast<const float4 *>(P + base + j);
+    const uint2 qh = *reinterpret_cast<const uint2 *>(qrow + j);
+    const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&qh.x));
+    const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&qh.y));
+    u.q[0] = lo.x; u.q[1] = lo.y; u.q[2] = hi.x; u.q[3] = hi.y;
+    if (terms > 1) {
+        const uint2 ql = *reinterpret_cast<const uint2 *>(qrow + ldq + j);
+        const float2 l2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&ql.x));
+        const float2 h2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&ql.y));
+        u.q[0] += l2.x; u.q[1] += l2.y; u.q[2] += h2.x; u.q[3] += h2.y;
+    }
+    return u;
+}
+
+__device__ __forceinline__ void ls_accumulate(const LsQuad &u, float &a1, float &a2, float &a3) {
+    const float d0 = u.q[0] - u.p.x, d1 = u.q[1] - u.p.y, d2 = u.q[2] - u.p.z, d3 = u.q[3] - u.p.w;
+    a1 += u.g.x * d0 + u.g.y * d1 + u.g.z * d2 + u.g.w * d3;
+    a2 += u.h.x * d0 + u.h.y * d1 + u.h.z * d2 + u.h.w * d3;
+    a3 += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+}
+
 // Per-block partial sums of <G, D>, <G_Q, D>, <D, D> with D = Q - P, where Q is
 // given either as BF16 split terms (the exact values the GEMMs consumed) or as
 // FP32.  One block per row at a time; FP32 within a row segment, FP64 across.
@@ -218,28 +251,17 @@ __global__ void __launch_bounds__(256) k_ls_partial(const float *__restrict__ G,
         const __nv_bfloat16 *qrow = Qb ? Qb + (long long)i * ((long long)terms * ldq) : nullptr;
         float a1 = 0.f, a2 = 0.f, a3 = 0.f;
         if (vec) {
-            for (int j = threadIdx.x * 4; j < n; j += blockDim.x * 4) {
-                const float4 g4 = *reinterpret_cast<const float4 *>(G + base + j);
-                const float4 h4 = *reinterpret_cast<const float4 *>(GQ + base + j);
-                const float4 p4 = *reinterpret_cast<const float4 *>(P + base + j);
-                const uint2 qh = *reinterpret_cast<const uint2 *>(qrow + j);
-                float q[4];
-                {
-                    const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&qh.x));
-                    const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&qh.y));
-                    q[0] = lo.x; q[1] = lo.y; q[2] = hi.x; q[3] = hi.y;
-                }
-                if (terms > 1) {
-                    const uint2 ql = *reinterpret_cast<const uint2 *>(qrow + ldq + j);
-                    const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&ql.x));
-                    const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&ql.y));
-                    q[0] += lo.x; q[1] += lo.y; q[2] += hi.x; q[3] += hi.y;
-                }
-                const float d0 = q[0] - p4.x, d1 = q[1] - p4.y, d2 = q[2] - p4.z, d3 = q[3] - p4.w;
-                a1 += g4.x * d0 + g4.y * d1 + g4.z * d2 + g4.w * d3;
-                a2 += h4.x * d0 + h4.y * d1 + h4.z * d2 + h4.w * d3;
-                a3 += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+            // two steps' loads in flight before either is accumulated; the terms
+            // are still added in the order of j
+            const int step = blockDim.x * 4;
+            int j = threadIdx.x * 4;
+            for (; j + step < n; j += 2 * step) {
+                const LsQuad u = ls_load(G, GQ, P, qrow, ldq, terms, base, j);
+                const LsQuad v = ls_load(G, GQ, P, qrow, ldq, terms, base, j + step);
+                ls_accumulate(u, a1, a2, a3);
+                ls_accumulate(v, a1, a2, a3);
             }
+            if (j < n) ls_accumulate(ls_load(G, GQ, P, qrow, ldq, terms, base, j), a1, a2, a3);
         } else {
             for (int j = threadIdx.x; j < n; j += blockDim.x) {
                 const float q = Qf ? Qf[base + j] : q_terms(qrow, ldq, terms, j);

@@ -57,22 +57,36 @@ __global__ void __launch_bounds__(256) k_sk_row(const float *__restrict__ G, int
         const float *Gi = G + (long long)row * ld;
         float m = -INFINITY, s = 0.0f;
         int j = lane * 4;
-        for (; j + 128 < n4; j += 256) {
-            const float4 a0 = __ldg(reinterpret_cast<const float4 *>(Gi + j));
-            const float4 a1 = __ldg(reinterpret_cast<const float4 *>(Gi + j + 128));
-            const float4 b0 = __ldg(reinterpret_cast<const float4 *>(g + j));
-            const float4 b1 = __ldg(reinterpret_cast<const float4 *>(g + j + 128));
-            const float x0 = (b0.x - a0.x) * c, x1 = (b0.y - a0.y) * c, x2 = (b0.z - a0.z) * c,
-                        x3 = (b0.w - a0.w) * c;
-            const float x4 = (b1.x - a1.x) * c, x5 = (b1.y - a1.y) * c, x6 = (b1.z - a1.z) * c,
-                        x7 = (b1.w - a1.w) * c;
-            const float mx = fmaxf(fmaxf(fmaxf(x0, x1), fmaxf(x2, x3)), fmaxf(fmaxf(x4, x5), fmaxf(x6, x7)));
-            if (mx > m) {
-                s *= fast_exp2(m - mx);
-                m = mx;
+        if (j + 128 < n4) {
+            // the next step's G loads are issued before this step's arithmetic
+            float4 a0 = __ldg(reinterpret_cast<const float4 *>(Gi + j));
+            float4 a1 = __ldg(reinterpret_cast<const float4 *>(Gi + j + 128));
+            for (;;) {
+                const int jn = j + 256;
+                const bool more = jn + 128 < n4;
+                float4 na0, na1;
+                const float4 b0 = __ldg(reinterpret_cast<const float4 *>(g + j));
+                const float4 b1 = __ldg(reinterpret_cast<const float4 *>(g + j + 128));
+                if (more) {
+                    na0 = __ldg(reinterpret_cast<const float4 *>(Gi + jn));
+                    na1 = __ldg(reinterpret_cast<const float4 *>(Gi + jn + 128));
+                }
+                const float x0 = (b0.x - a0.x) * c, x1 = (b0.y - a0.y) * c, x2 = (b0.z - a0.z) * c,
+                            x3 = (b0.w - a0.w) * c;
+                const float x4 = (b1.x - a1.x) * c, x5 = (b1.y - a1.y) * c, x6 = (b1.z - a1.z) * c,
+                            x7 = (b1.w - a1.w) * c;
+                const float mx = fmaxf(fmaxf(fmaxf(x0, x1), fmaxf(x2, x3)), fmaxf(fmaxf(x4, x5), fmaxf(x6, x7)));
+                if (mx > m) {
+                    s *= fast_exp2(m - mx);
+                    m = mx;
+                }
+                s += fast_exp2(x0 - m) + fast_exp2(x1 - m) + fast_exp2(x2 - m) + fast_exp2(x3 - m) +
+                     fast_exp2(x4 - m) + fast_exp2(x5 - m) + fast_exp2(x6 - m) + fast_exp2(x7 - m);
+                j = jn;
+                if (!more) break;
+                a0 = na0;
+                a1 = na1;
             }
-            s += fast_exp2(x0 - m) + fast_exp2(x1 - m) + fast_exp2(x2 - m) + fast_exp2(x3 - m) +
-                 fast_exp2(x4 - m) + fast_exp2(x5 - m) + fast_exp2(x6 - m) + fast_exp2(x7 - m);
         }
         for (; j < n4; j += 128) {
             const float4 a0 = __ldg(reinterpret_cast<const float4 *>(Gi + j));
@@ -95,29 +109,30 @@ __global__ void __launch_bounds__(256) k_sk_row(const float *__restrict__ G, int
 
 // ---------------------------------------------------------------- column sums
 
-// Partial column sums over a chunk of rows; each thread owns 4 adjacent columns.
-// Terms are summed in FP32 in groups of 16 rows and the groups in FP64.
-__global__ void __launch_bounds__(256) k_sk_colpart(const float *__restrict__ G, int n, long long ld,
-                                                    const float *__restrict__ f, const float *__restrict__ g,
-                                                    double *__restrict__ partial, int rows_per_chunk,
-                                                    const DevState *__restrict__ st) {
-    if (st->sk_done) return;
-    const float c = st->c;
-    const int j0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    const int r0 = blockIdx.y * rows_per_chunk;
-    const int r1 = min(n, r0 + rows_per_chunk);
-    if (j0 >= n) return;
-    const bool vec = (j0 + 3 < n) && ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(G) & 15) == 0);
+// Partial column sums over a chunk of rows.  A CTA owns 2048 adjacent columns:
+// each lane owns two groups of 4 columns 128 columns apart, so a warp reads two
+// contiguous 512-byte runs (1 KB) of every row and keeps 2 rows x 2 float4 loads
+// in flight.  Every column is summed the same way whatever the launch shape:
+// FP32 over groups of 16 rows (from the chunk's first row), the groups in FP64.
+// EDGE = false is launched only on CTAs whose 2048 columns all lie inside the
+// matrix with G 16-byte aligned, and carries no other path (the fallback code
+// alone, even at the same register count, cost 10 % of the pass).  EDGE = true
+// covers the rest: a group of 4 columns cut by the matrix edge, or any group
+// of a G that is not 16-byte aligned, takes the scalar path (FP64 per term).
+constexpr int kSkColsPerCta = 2048;
+
+__device__ __forceinline__ void colpart_group(const float *__restrict__ G, int n, long long ld,
+                                              const float *__restrict__ f, const float *__restrict__ g, float c,
+                                              int j0, int r0, int r1, bool aligned, double *__restrict__ dst) {
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     float gj[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) gj[k] = (j0 + k < n) ? __ldg(g + j0 + k) : 0.0f;
-    if (vec) {
+    if (aligned && j0 + 3 < n) {
         int i = r0;
         while (i < r1) {
             const int ie = min(r1, i + 16);
             float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll 4
             for (; i < ie; ++i) {
                 const float4 a = __ldg(reinterpret_cast<const float4 *>(G + (long long)i * ld + j0));
                 const float fi = __ldg(f + i);
@@ -139,10 +154,66 @@ __global__ void __launch_bounds__(256) k_sk_colpart(const float *__restrict__ G,
                 if (j0 + k < n) acc[k] += fast_exp2((fi + gj[k] - __ldg(G + (long long)i * ld + j0 + k)) * c);
         }
     }
-    double *dst = partial + (long long)blockIdx.y * n + j0;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-        if (j0 + k < n) dst[k] = acc[k];
+        if (j0 + k < n) dst[j0 + k] = acc[k];
+}
+
+template <bool EDGE>
+__global__ void __launch_bounds__(256) k_sk_colpart(const float *__restrict__ G, int n, long long ld,
+                                                    const float *__restrict__ f, const float *__restrict__ g,
+                                                    double *__restrict__ partial, int rows_per_chunk, int col0,
+                                                    const DevState *__restrict__ st) {
+    if (st->sk_done) return;
+    const float c = st->c;
+    const int ja = col0 + blockIdx.x * kSkColsPerCta + (threadIdx.x >> 5) * 256 + (threadIdx.x & 31) * 4;
+    const int jb = ja + 128;
+    const int r0 = blockIdx.y * rows_per_chunk;
+    const int r1 = min(n, r0 + rows_per_chunk);
+    double *dst = partial + (long long)blockIdx.y * n;
+    if (EDGE) {
+        if (ja >= n) return;
+        const bool aligned = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(G) & 15) == 0);
+        if (!(aligned && jb + 3 < n)) {
+            colpart_group(G, n, ld, f, g, c, ja, r0, r1, aligned, dst);
+            if (jb < n) colpart_group(G, n, ld, f, g, c, jb, r0, r1, aligned, dst);
+            return;
+        }
+    }
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    float gj[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        gj[k] = __ldg(g + ja + k);
+        gj[4 + k] = __ldg(g + jb + k);
+    }
+    int i = r0;
+    while (i < r1) {
+        const int ie = min(r1, i + 16);
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+        for (; i < ie; ++i) {
+            const float *Gi = G + (long long)i * ld;
+            const float4 a = __ldg(reinterpret_cast<const float4 *>(Gi + ja));
+            const float4 b = __ldg(reinterpret_cast<const float4 *>(Gi + jb));
+            const float fi = __ldg(f + i);
+            s[0] += fast_exp2((fi + gj[0] - a.x) * c);
+            s[1] += fast_exp2((fi + gj[1] - a.y) * c);
+            s[2] += fast_exp2((fi + gj[2] - a.z) * c);
+            s[3] += fast_exp2((fi + gj[3] - a.w) * c);
+            s[4] += fast_exp2((fi + gj[4] - b.x) * c);
+            s[5] += fast_exp2((fi + gj[5] - b.y) * c);
+            s[6] += fast_exp2((fi + gj[6] - b.z) * c);
+            s[7] += fast_exp2((fi + gj[7] - b.w) * c);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] += s[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        dst[ja + k] = acc[k];
+        dst[jb + k] = acc[4 + k];
+    }
 }
 
 // Combines the chunk partials, takes the residual and applies the column scaling.
@@ -224,24 +295,41 @@ __global__ void k_sk_begin(DevState *st, float eps, float tol, float *g_zero, in
 
 // Q_ij = 2^(c (f_i + g_j - G_ij)), written as BF16 split terms (hi, and lo when
 // terms == 2) into the GEMM operand buffer, zero in the padding columns, and
-// optionally as FP32.
-__global__ void __launch_bounds__(256) k_write_q(const float *__restrict__ G, int n, long long ld,
-                                                 const float *__restrict__ f, const float *__restrict__ g,
-                                                 const DevState *__restrict__ st, __nv_bfloat16 *__restrict__ Qb,
-                                                 int ldq, int terms, float *__restrict__ Qf, long long ldf) {
-    const float c = st->c;
-    const int chunks = ldq / 8;  // 8 columns per thread
-    const long long total = (long long)n * chunks;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
+// optionally as FP32.  A thread writes 8 columns of a row: two float4 loads of G
+// and of g where the 8 columns lie inside the row and G is 16-byte aligned,
+// scalar loads at the edge; 32-bit index arithmetic when the chunk count fits.
+template <typename Idx>
+__device__ __forceinline__ void write_q_body(const float *__restrict__ G, int n, long long ld,
+                                             const float *__restrict__ f, const float *__restrict__ g, float c,
+                                             __nv_bfloat16 *__restrict__ Qb, int ldq, int terms, float *__restrict__ Qf,
+                                             long long ldf, bool vec) {
+    const Idx chunks = (Idx)(ldq / 8);  // 8 columns per thread
+    const Idx total = (Idx)n * chunks;
+    for (Idx t = (Idx)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (Idx)gridDim.x * blockDim.x) {
         const int i = (int)(t / chunks);
-        const int j0 = (int)(t - (long long)i * chunks) * 8;
+        const int j0 = (int)(t - (Idx)i * chunks) * 8;
         const float fi = __ldg(f + i);
+        const float *Gi = G + (long long)i * ld;
         float q[8];
+        if (vec && j0 + 7 < n) {
+            const float4 a0 = __ldg(reinterpret_cast<const float4 *>(Gi + j0));
+            const float4 a1 = __ldg(reinterpret_cast<const float4 *>(Gi + j0 + 4));
+            const float4 b0 = __ldg(reinterpret_cast<const float4 *>(g + j0));
+            const float4 b1 = __ldg(reinterpret_cast<const float4 *>(g + j0 + 4));
+            q[0] = fast_exp2((fi + b0.x - a0.x) * c);
+            q[1] = fast_exp2((fi + b0.y - a0.y) * c);
+            q[2] = fast_exp2((fi + b0.z - a0.z) * c);
+            q[3] = fast_exp2((fi + b0.w - a0.w) * c);
+            q[4] = fast_exp2((fi + b1.x - a1.x) * c);
+            q[5] = fast_exp2((fi + b1.y - a1.y) * c);
+            q[6] = fast_exp2((fi + b1.z - a1.z) * c);
+            q[7] = fast_exp2((fi + b1.w - a1.w) * c);
+        } else {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int j = j0 + k;
-            q[k] = (j < n) ? fast_exp2((fi + __ldg(g + j) - __ldg(G + (long long)i * ld + j)) * c) : 0.0f;
+            for (int k = 0; k < 8; ++k) {
+                const int j = j0 + k;
+                q[k] = (j < n) ? fast_exp2((fi + __ldg(g + j) - __ldg(Gi + j)) * c) : 0.0f;
+            }
         }
         uint32_t hw[4], lw[4];
 #pragma unroll
@@ -265,6 +353,19 @@ __global__ void __launch_bounds__(256) k_write_q(const float *__restrict__ G, in
     }
 }
 
+__global__ void __launch_bounds__(256) k_write_q(const float *__restrict__ G, int n, long long ld,
+                                                 const float *__restrict__ f, const float *__restrict__ g,
+                                                 const DevState *__restrict__ st, __nv_bfloat16 *__restrict__ Qb,
+                                                 int ldq, int terms, float *__restrict__ Qf, long long ldf) {
+    const float c = st->c;
+    const bool vec = ((ld & 3) == 0) && (((reinterpret_cast<uintptr_t>(G) | reinterpret_cast<uintptr_t>(g)) & 15) == 0);
+    const long long total = (long long)n * (ldq / 8);
+    if (total + (long long)gridDim.x * blockDim.x < 0xffffffffLL)
+        write_q_body<unsigned>(G, n, ld, f, g, c, Qb, ldq, terms, Qf, ldf, vec);
+    else
+        write_q_body<long long>(G, n, ld, f, g, c, Qb, ldq, terms, Qf, ldf, vec);
+}
+
 // ---------------------------------------------------------------- host driver
 
 struct SinkhornLaunch {
@@ -277,9 +378,14 @@ static SinkhornLaunch sinkhorn_launch(int n) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     SinkhornLaunch L;
     L.row_grid = (int)std::min<int64_t>(ceil_div(n, 8), (int64_t)sms * 16);
-    L.colpart_x = (int)ceil_div(n, 1024);
-    const int target = sms * 8;
-    int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(target, L.colpart_x), ceil_div(n, 64)));
+    // column pass: as many row chunks as fill one wave of resident CTAs (a second,
+    // partial wave would leave most SMs idle at its end), at least 64 rows each
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sk_colpart<false>, 256, 0) != cudaSuccess || occ < 1)
+        occ = 4;
+    L.colpart_x = (int)ceil_div(n, kSkColsPerCta);
+    const int64_t slots = (int64_t)sms * occ;
+    int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(slots / L.colpart_x, ceil_div(n, 64)));
     L.rows_per_chunk = (int)ceil_div(n, chunks);
     L.colpart_y = (int)ceil_div(n, L.rows_per_chunk);
     L.final_grid = (int)ceil_div(n, 256);
@@ -291,12 +397,27 @@ long long sinkhorn_partial_elems(int n) {
     return (long long)L.colpart_y * n;
 }
 
+// Queues the column pass: full, aligned 2048-column CTAs take the fallback-free
+// instantiation, the rest (a ragged right edge, or all of an unaligned G) the
+// general one.  Returns the number of launches.
+static int sinkhorn_colpart(const float *G, int n, long long ld, const float *f, const float *g, double *partial,
+                            const DevState *st, const SinkhornLaunch &L, cudaStream_t s) {
+    const bool aligned = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(G) & 15) == 0);
+    const int full = aligned ? n / kSkColsPerCta : 0;
+    const int edge = L.colpart_x - full;
+    if (full > 0)
+        k_sk_colpart<false><<<dim3(full, L.colpart_y), 256, 0, s>>>(G, n, ld, f, g, partial, L.rows_per_chunk, 0, st);
+    if (edge > 0)
+        k_sk_colpart<true><<<dim3(edge, L.colpart_y), 256, 0, s>>>(G, n, ld, f, g, partial, L.rows_per_chunk,
+                                                                    full * kSkColsPerCta, st);
+    return (full > 0) + (edge > 0);
+}
+
 // Queues one Sinkhorn iteration.
 static void sinkhorn_iteration(const float *G, int n, long long ld, float *f, float *g, double *partial,
                                DevState *st, int max_iter, const SinkhornLaunch &L, cudaStream_t s) {
-    note_launches(4);
     k_sk_row<<<L.row_grid, 256, 0, s>>>(G, n, ld, g, f, st);
-    k_sk_colpart<<<dim3(L.colpart_x, L.colpart_y), 256, 0, s>>>(G, n, ld, f, g, partial, L.rows_per_chunk, st);
+    note_launches(3 + sinkhorn_colpart(G, n, ld, f, g, partial, st, L, s));
     k_sk_colfinal<<<L.final_grid, 256, 0, s>>>(partial, L.colpart_y, n, G, ld, f, g, st);
     k_sk_check<<<1, 1, 0, s>>>(st, max_iter);
 }
