@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--pairs", type=int, default=512)
     ap.add_argument("--restarts", type=int, default=20)
     ap.add_argument("--train-pairs", type=int, default=48)
-    ap.add_argument("--kernel-case", choices=["gemm", "sinkhorn", "lap", "batched", "warmstart"], default=None,
+    ap.add_argument("--kernel-case", choices=["gemm", "sinkhorn", "lap", "batched", "warmstart", "lot", "faq"],
+                    default=None,
                     help="run only one step kind a few times on the workload (the small cases profiled with ncu)")
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--precision", choices=["bf16", "fp8", "fp32"], default="bf16",
@@ -241,7 +242,9 @@ def run_kernel_case(args):
     gemm:     goat_gradient at a doubly stochastic P (two tensor-core products per call)
     sinkhorn: goat_sinkhorn on -grad f(J) for a fixed number of iterations (tol 0)
     lap:      goat_project on the entropic direction Q at the barycenter (a diffuse,
-              degree-structured doubly stochastic matrix like the relaxed P of a hard pair)"""
+              degree-structured doubly stochastic matrix like the relaxed P of a hard pair)
+    faq:      one goat_match solve with the LOT direction (GOAT, Alg. 3) and one with the
+              exact assignment direction (FAQ, Alg. 1), --precision form, on the same pair"""
     import torch
 
     import paper_2111_05366_gb300 as goat
@@ -252,6 +255,8 @@ def run_kernel_case(args):
         return run_batched_case(args)
     if args.kernel_case == "warmstart":
         return run_warmstart_case(args)
+    if args.kernel_case == "lot":
+        return run_lot_case(args)
     n = args.n
     gp = synthetic.large_sbm_pair(n, seed=args.seed)
     A = torch.from_numpy(gp.A).cuda()
@@ -269,6 +274,25 @@ def run_kernel_case(args):
             goat.goat_gradient(A, B, P, precision=prec, out=G)
         e1.record()
         out["precision"] = args.precision
+    elif args.kernel_case == "faq":
+        prec = {"bf16": goat.GOAT_PREC_BF16, "fp8": goat.GOAT_PREC_FP8, "fp32": goat.GOAT_PREC_FP32}[args.precision]
+        del P
+        out["precision"] = args.precision
+        for name, direction in (("goat", goat.GOAT_DIR_LOT), ("faq", goat.GOAT_DIR_LAP)):
+            prm = goat.default_params(precision=prec, sk_warm_start=1, sk_tol=args.sk_tol,
+                                      sk_max_iter=args.sk_max_iter, profile=1, direction=direction)
+            torch.cuda.synchronize()
+            e0.record()
+            perm, obj, st = goat.goat_match(A, B, eps_rel=0.03, max_iter=args.max_iter, tol=args.fw_tol, params=prm)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out[name] = {"ms_solve": ms, "fw_iters": st["fw_iters"], "converged": st["converged"],
+                         "fw_iters_per_s": st["fw_iters"] / (ms / 1000.0),
+                         "ms_direction_steps": st["ms_sinkhorn"], "ms_products": st["ms_gemm"],
+                         "ms_projection": st["ms_project"], "accuracy": float((perm == gp.truth).mean()),
+                         "objective": obj}
+            log(f"{name}: {st['fw_iters']} FW iterations in {ms:.0f} ms, accuracy {out[name]['accuracy']:.4f}")
     elif args.kernel_case == "sinkhorn":
         G = goat.goat_gradient(A, B, P)
         eps = 0.03 * float(G.abs().max())
@@ -289,8 +313,54 @@ def run_kernel_case(args):
         e1.record()
         out["cost"], out["gap"], out["info"] = cost, gap, info
     torch.cuda.synchronize()
-    out["ms_per_call"] = e0.elapsed_time(e1) / args.repeat
+    if args.kernel_case != "faq":
+        out["ms_per_call"] = e0.elapsed_time(e1) / args.repeat
     print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_lot_case(args):
+    """LOT against exact linear assignment on the paper's Fig. 1 workload (Sec. 3.3):
+    i.i.d. Uniform(100, 150) costs, n = 250, 500, ..., 3000, lambda = 100 (eps = 0.01),
+    --repeat matrices per n.  Per n: the device time of goat_sinkhorn to the marginal
+    tolerance --sk-tol (Q written out) and of goat_project (certified optimum), and the
+    relative objective gap (OFV_LAP - OFV_LOT) / OFV_LAP of the paper's Fig. 1."""
+    import torch
+
+    import paper_2111_05366_gb300 as goat
+    from paper_2111_05366_gb300 import synthetic
+    eps = 0.01
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    rows = []
+    for n in range(250, 3001, 250):
+        lot_ms, lap_ms, gaps, iters = [], [], [], []
+        for k in range(args.repeat + 1):  # k = 0 warms up this size
+            M = torch.from_numpy(synthetic.uniform_costs(n, 100, 150, 1000 * n + k, np.float32)).cuda()
+            (_, _, Q, it, resid), t_lot = timed(lambda: goat.goat_sinkhorn(M, eps, args.sk_tol, 5000, want_Q=True))
+            (_, cost, _), t_lap = timed(lambda: goat.goat_project(M, maximize=False))
+            ofv = float((Q.double() * M.double()).sum())
+            if k:
+                lot_ms.append(t_lot)
+                lap_ms.append(t_lap)
+                gaps.append((cost - ofv) / cost)
+                iters.append(it)
+        rows.append({"n": n, "lot_ms": float(np.mean(lot_ms)), "lap_ms": float(np.mean(lap_ms)),
+                     "lap_over_lot": float(np.mean(lap_ms) / np.mean(lot_ms)),
+                     "max_abs_rel_gap": float(np.max(np.abs(gaps))), "mean_rel_gap": float(np.mean(gaps)),
+                     "lot_iters": float(np.mean(iters))})
+        log(f"n={n}: LOT {rows[-1]['lot_ms']:.2f} ms ({rows[-1]['lot_iters']:.0f} it), "
+            f"LAP {rows[-1]['lap_ms']:.2f} ms, gap {rows[-1]['max_abs_rel_gap']:.2e}")
+    print(json.dumps({"case": "lot_vs_lap", "costs": "Uniform(100, 150)", "eps": eps, "lambda": 1.0 / eps,
+                      "sk_tol": args.sk_tol, "matrices_per_n": args.repeat, "rows": rows}), flush=True)
     return 0
 
 
@@ -456,7 +526,8 @@ def main():
     n = args.n
     log(f"generating the n={n} pair")
     gp = synthetic.large_sbm_pair(n, seed=args.seed + rank)
-    log(f"pair ready: {int(gp.A.sum())} + {int(gp.B.sum())} nonzeros")
+    nnz_A, nnz_B = int(gp.A.sum()), int(gp.B.sum())
+    log(f"pair ready: {nnz_A} + {nnz_B} nonzeros")
     A = torch.from_numpy(gp.A).cuda()
     B = torch.from_numpy(gp.B).cuda()
     ws = torch.empty(max(goat.workspace_bytes(n, goat.GOAT_DTYPE_U8, pr) for pr in
@@ -528,10 +599,15 @@ def main():
         kernel = "k_gemm_xyT (BF16 kind::f16, one n x n x n product per launch)"
         peak_source = f"{peaks['source']} bf16_tflops_sustained"
         traffic = gemm_traffic_per_launch(n)
+    # A and B are ~1 % dense: the products do 2 n^3 dense FLOP, of which only
+    # 2 nnz(B) n (C1 = B Q^T) and 2 nnz(A) n (A C1^T) multiply a nonzero
+    useful_per_launch = float(nnz_A + nnz_B) * n
     roofline = {"bound": "tensor", "kernel": kernel,
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_source,
-                "algorithmic_flop_per_launch": flop_per_launch}
+                "algorithmic_flop_per_launch": flop_per_launch,
+                "useful_flop_per_launch": useful_per_launch,
+                "useful_tflops": useful_per_launch / (ms_gemm / max(n_gemm, 1) / 1000.0) / 1e12}
 
     ms_fw_loop = sum(o[2]["ms_fw"] for o in outs)
     breakdown = {"ms_per_fw_iter": ms / max(fw_iters, 1), "gemm_ms_per_launch": ms_gemm / max(n_gemm, 1),

@@ -86,6 +86,16 @@ enum {
     GOAT_PREC_FP8 = 2
 };
 
+/* direction step of each Frank-Wolfe iteration (goat_params.direction) */
+enum {
+    /* GOAT (Alg. 3): the entropic optimal-transport (LOT, Alg. 2) solution Q on
+     * -grad f(P), a doubly stochastic matrix */
+    GOAT_DIR_LOT = 0,
+    /* FAQ (Alg. 1): an exact linear assignment, the permutation maximising
+     * <Pi, grad f(P)>, by the same solver as the final projection */
+    GOAT_DIR_LAP = 1
+};
+
 #define GOAT_TRACE_MAX 256
 
 /* Parameters of the warm-start network (W1 [64][8], b1 [64], w2 [64], b2). */
@@ -104,6 +114,12 @@ typedef struct goat_params {
      * Sinkhorn solve of goat_match starts from the duals the network predicts; if
      * that solve fails to reach sk_tol it is redone from a cold start. */
     const void *mlp_weights;
+    /* GOAT_DIR_LOT (default: GOAT) or GOAT_DIR_LAP (FAQ).  With GOAT_DIR_LAP the
+     * sk_* fields and mlp_weights are unused, stats.sk_iters are 0 and
+     * stats.ms_sinkhorn times the per-iteration assignments; an assignment that the
+     * auction cannot certify within its budget is still a permutation and is used.
+     * goat_match_batched takes GOAT_DIR_LOT only. */
+    int direction;
 } goat_params;
 
 typedef struct goat_stats {
@@ -146,7 +162,8 @@ GOAT_API size_t goat_workspace_bytes(int n, int dtype_AB, int precision);
 GOAT_API size_t goat_workspace_bytes_host(int n, int dtype_AB, int precision);
 
 /*
- * goat_match -- the whole GOAT solve (Alg. 3).
+ * goat_match -- the whole GOAT solve (Alg. 3), or FAQ (Alg. 1) with
+ * p->direction = GOAT_DIR_LAP.
  *   A, B       device, n x n, dtype_AB, symmetric, zero diagonal (checked:
  *              GOAT_ERR_INVALID_ARG otherwise).
  *   init       device n x n float doubly stochastic start, or NULL for the

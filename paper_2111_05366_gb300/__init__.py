@@ -33,6 +33,8 @@ GOAT_DTYPE_F32 = 1
 GOAT_PREC_BF16 = 0
 GOAT_PREC_FP32 = 1
 GOAT_PREC_FP8 = 2
+GOAT_DIR_LOT = 0  # GOAT (Alg. 3): entropic OT direction
+GOAT_DIR_LAP = 1  # FAQ (Alg. 1): exact linear-assignment direction
 GOAT_TRACE_MAX = 256
 GOAT_MLP_PARAMS = 641
 
@@ -54,7 +56,7 @@ class goat_params(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("sk_max_iter", ctypes.c_int), ("sk_tol", ctypes.c_float),
                 ("sk_warm_start", ctypes.c_int), ("sk_check_every", ctypes.c_int),
                 ("project_on_grad", ctypes.c_int), ("lap_max_rounds", ctypes.c_int), ("profile", ctypes.c_int),
-                ("mlp_weights", ctypes.c_void_p)]
+                ("mlp_weights", ctypes.c_void_p), ("direction", ctypes.c_int)]
 
 
 class goat_stats(ctypes.Structure):
@@ -220,7 +222,8 @@ def _stats_dict(st: goat_stats) -> dict:
 
 def goat_match(A, B, init=None, eps_rel: float = 0.03, max_iter: int = 30, tol: float = 0.03,
                params: goat_params | None = None, workspace=None):
-    """Whole GOAT solve (Alg. 3) on device tensors A, B (n x n, uint8 or float32).
+    """Whole GOAT solve (Alg. 3) on device tensors A, B (n x n, uint8 or float32), or
+    FAQ (Alg. 1) with params.direction = GOAT_DIR_LAP.
 
     Returns (perm int32 numpy [n], objective, stats dict)."""
     n = A.shape[0]

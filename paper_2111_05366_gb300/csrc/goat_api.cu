@@ -335,36 +335,58 @@ static int match_impl(const void *A, const void *B, int n, int dtype, const floa
     float ms_gemm = 0.f, ms_sk = 0.f, ms_step = 0.f;
     int gemm_launches = 0;
 
+    // the LAP schedule: FAQ's per-iteration directions and the final projection
+    LapControl ctl;
+    lap_default_control(&ctl);
+    ctl.max_rounds = prm.lap_max_rounds;
+    const bool faq = prm.direction == GOAT_DIR_LAP;
+
     int it = 0, converged = 0;
     for (; it < max_iter; ++it) {
         if (prof) cudaEventRecord(pe[0], s);
-        const bool learned = it == 0 && prm.mlp_weights;
-        if (learned) {
-            // the learned warm start needs this step's eps on the host: eps_rel * max|G|
-            GOAT_TRY(cuda_status(cudaMemcpyAsync(pinned, &st->gmax_bits, sizeof(unsigned), cudaMemcpyDeviceToHost, s)));
-            GOAT_TRY(cuda_status(cudaStreamSynchronize(s)));
-            float gm;
-            std::memcpy(&gm, pinned, sizeof(float));
-            float e0 = eps_rel * gm;
-            if (!(e0 > 0.f)) e0 = 1.0f;
-            GOAT_TRY(mlp_warm_start_g(G, A, B, n, dtype, e0, (const __nv_bfloat16 *)prm.mlp_weights, g,
-                                      ws.at<float>(w.mlp), s));
-        }
-        sinkhorn_begin(st, -1.0f, prm.sk_tol, (prm.sk_warm_start || learned) ? nullptr : g, n, s);
-        GOAT_TRY(sinkhorn_solve(G, n, n, f, g, partial, st, prm.sk_max_iter, prm.sk_check_every, pinned, s));
-        if (learned) {
-            // fallback: a learned start that does not reach the tolerance is redone cold
-            GOAT_TRY(cuda_status(cudaMemcpyAsync(pinned, &st->sk_resid, sizeof(float), cudaMemcpyDeviceToHost, s)));
-            GOAT_TRY(cuda_status(cudaStreamSynchronize(s)));
-            float r;
-            std::memcpy(&r, pinned, sizeof(float));
-            if (!(r < prm.sk_tol)) {
-                sinkhorn_begin(st, -1.0f, prm.sk_tol, g, n, s);
-                GOAT_TRY(sinkhorn_solve(G, n, n, f, g, partial, st, prm.sk_max_iter, prm.sk_check_every, pinned, s));
+        if (faq) {
+            // FAQ (Alg. 1): Q = argmax over permutations of <Pi, grad f(P)> = argmin <Pi, G>;
+            // an uncertified assignment is still a permutation, so it is used
+            LapReport drep{};
+            double dgap = 0.0;
+            const int dst = lap_solve(G, n, 0, perm_dev, ws.at<void>(w.lap), st, ctl, ws.at<double>(w.cost) + 6,
+                                      pinned, &dgap, &drep, s);
+            if (dst != GOAT_OK && dst != GOAT_ERR_NOT_CONVERGED) return dst;
+            if (prof) cudaEventRecord(pe[1], s);
+            GOAT_TRY(write_perm_q(perm_dev, n, Xq, w.ld, w.terms, s));
+        } else {
+            // GOAT (Alg. 3): Q = LOT(-grad f(P)) (Alg. 2)
+            const bool learned = it == 0 && prm.mlp_weights;
+            if (learned) {
+                // the learned warm start needs this step's eps on the host: eps_rel * max|G|
+                GOAT_TRY(cuda_status(
+                    cudaMemcpyAsync(pinned, &st->gmax_bits, sizeof(unsigned), cudaMemcpyDeviceToHost, s)));
+                GOAT_TRY(cuda_status(cudaStreamSynchronize(s)));
+                float gm;
+                std::memcpy(&gm, pinned, sizeof(float));
+                float e0 = eps_rel * gm;
+                if (!(e0 > 0.f)) e0 = 1.0f;
+                GOAT_TRY(mlp_warm_start_g(G, A, B, n, dtype, e0, (const __nv_bfloat16 *)prm.mlp_weights, g,
+                                          ws.at<float>(w.mlp), s));
             }
+            sinkhorn_begin(st, -1.0f, prm.sk_tol, (prm.sk_warm_start || learned) ? nullptr : g, n, s);
+            GOAT_TRY(sinkhorn_solve(G, n, n, f, g, partial, st, prm.sk_max_iter, prm.sk_check_every, pinned, s));
+            if (learned) {
+                // fallback: a learned start that does not reach the tolerance is redone cold
+                GOAT_TRY(
+                    cuda_status(cudaMemcpyAsync(pinned, &st->sk_resid, sizeof(float), cudaMemcpyDeviceToHost, s)));
+                GOAT_TRY(cuda_status(cudaStreamSynchronize(s)));
+                float r;
+                std::memcpy(&r, pinned, sizeof(float));
+                if (!(r < prm.sk_tol)) {
+                    sinkhorn_begin(st, -1.0f, prm.sk_tol, g, n, s);
+                    GOAT_TRY(
+                        sinkhorn_solve(G, n, n, f, g, partial, st, prm.sk_max_iter, prm.sk_check_every, pinned, s));
+                }
+            }
+            if (prof) cudaEventRecord(pe[1], s);
+            write_q(G, n, n, f, g, st, Xq, w.ld, w.terms, nullptr, 0, s);
         }
-        if (prof) cudaEventRecord(pe[1], s);
-        write_q(G, n, n, f, g, st, Xq, w.ld, w.terms, nullptr, 0, s);
         if (prof) cudaEventRecord(pe[2], s);
         GOAT_TRY(gradient_from_terms(w, ws, n, GQ, &st->error, s, prof ? pe[3] : nullptr));
         if (prof) cudaEventRecord(pe[4], s);
@@ -398,9 +420,6 @@ static int match_impl(const void *A, const void *B, int n, int dtype, const floa
 
     // projection onto the permutations
     double gap = 0.0;
-    LapControl ctl;
-    lap_default_control(&ctl);
-    ctl.max_rounds = prm.lap_max_rounds;
     LapReport rep{};
     int lst;
     if (prm.project_on_grad) {
@@ -483,6 +502,7 @@ static goat_params resolve_params(const goat_params *p) {
 }
 
 static bool valid_precision(int p) { return p == GOAT_PREC_BF16 || p == GOAT_PREC_FP32 || p == GOAT_PREC_FP8; }
+static bool valid_direction(int d) { return d == GOAT_DIR_LOT || d == GOAT_DIR_LAP; }
 static bool valid_dtype(int d) { return d == GOAT_DTYPE_U8 || d == GOAT_DTYPE_F32; }
 
 }  // namespace goat
@@ -503,6 +523,7 @@ void goat_default_params(goat_params *p) {
     p->sk_check_every = 8;
     p->project_on_grad = 0;
     p->lap_max_rounds = 1 << 20;
+    p->direction = GOAT_DIR_LOT;
 }
 
 const char *goat_strerror(int status) {
@@ -536,7 +557,7 @@ int goat_match(const void *A, const void *B, int n, int dtype_AB, const float *i
         !(tol >= 0.0f) || max_iter > (1 << 20))
         return GOAT_ERR_INVALID_ARG;
     const goat_params prm = resolve_params(p);
-    if (!valid_precision(prm.precision)) return GOAT_ERR_INVALID_ARG;
+    if (!valid_precision(prm.precision) || !valid_direction(prm.direction)) return GOAT_ERR_INVALID_ARG;
     GOAT_TRY(device_ok());
     cudaStream_t s = (cudaStream_t)stream;
     const Plan w = make_plan(n, dtype_AB, prm.precision, NEED_FW);
@@ -554,7 +575,7 @@ int goat_match_host(const void *A_host, const void *B_host, int n, int dtype_AB,
         !(tol >= 0.0f))
         return GOAT_ERR_INVALID_ARG;
     const goat_params prm = resolve_params(p);
-    if (!valid_precision(prm.precision)) return GOAT_ERR_INVALID_ARG;
+    if (!valid_precision(prm.precision) || !valid_direction(prm.direction)) return GOAT_ERR_INVALID_ARG;
     GOAT_TRY(device_ok());
     cudaStream_t s = (cudaStream_t)stream;
     // the device copies sit after the goat_match layout, so a goat_match-sized

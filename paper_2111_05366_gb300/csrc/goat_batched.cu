@@ -657,6 +657,7 @@ int goat_match_batched(const void *A, const void *B, const long long *adj_off, c
     goat_params prm;
     goat_default_params(&prm);
     if (params) prm = *params;
+    if (prm.direction != GOAT_DIR_LOT) return GOAT_ERR_INVALID_ARG;  // the batched path runs GOAT only
     if (prm.sk_max_iter <= 0) prm.sk_max_iter = 500;
     if (!(prm.sk_tol > 0.f)) prm.sk_tol = 1e-3f;
     int dev = 0, major = 0, minor = 0, sms = 148;

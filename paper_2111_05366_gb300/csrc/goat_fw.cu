@@ -555,6 +555,24 @@ void absmax(const float *X, long long total, unsigned *out, cudaStream_t s) {
     k_absmax<<<grid_for(total), 256, 0, s>>>(X, total, out);
 }
 
+// FAQ's direction (Alg. 1): Q = the permutation matrix of perm (Q[i][perm i] = 1),
+// as BF16 terms in the GEMM operand buffer, which the caller zeroed.
+__global__ void __launch_bounds__(256) k_write_perm_q(const int32_t *__restrict__ perm, int n,
+                                                      __nv_bfloat16 *__restrict__ Qb, int ldq, int terms) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int j = perm[i];
+        if (j >= 0 && j < n) Qb[(long long)i * ((long long)terms * ldq) + j] = __float2bfloat16(1.0f);
+    }
+}
+
+int write_perm_q(const int32_t *perm, int n, __nv_bfloat16 *Qb, int ldq, int terms, cudaStream_t s) {
+    if (cudaMemsetAsync(Qb, 0, (size_t)n * terms * ldq * sizeof(__nv_bfloat16), s) != cudaSuccess)
+        return GOAT_ERR_CUDA;
+    note_launches(1);
+    k_write_perm_q<<<(int)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, s>>>(perm, n, Qb, ldq, terms);
+    return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
+}
+
 int ls_blocks(int n) { return rows_grid(n, 4); }
 
 void line_search(const float *G, const float *GQ, const float *P, const __nv_bfloat16 *Qb, int ldq, int terms,

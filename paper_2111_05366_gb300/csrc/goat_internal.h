@@ -125,6 +125,8 @@ int sinkhorn_solve(const float *G, int n, long long ld, float *f, float *g, doub
                    int max_iter, int check_every, int *host_flag, cudaStream_t s);
 void sinkhorn_queue_fixed(const float *G, int n, long long ld, float *f, float *g, double *partial, DevState *st,
                           int max_iter, cudaStream_t s);
+// Zeroes the operand buffer and writes the permutation matrix of perm into it (FAQ's Q).
+int write_perm_q(const int32_t *perm, int n, __nv_bfloat16 *Qb, int ldq, int terms, cudaStream_t s);
 void write_q(const float *G, int n, long long ld, const float *f, const float *g, const DevState *st,
              __nv_bfloat16 *Qb, int ldq, int terms, float *Qf, long long ldf, cudaStream_t s);
 

@@ -46,7 +46,31 @@ def test_host_only_calls(lib_path):
     assert "sm_103" in goat.strerror(goat.GOAT_ERR_UNSUPPORTED)
     p = goat.default_params()
     assert p.sk_max_iter == 500 and abs(p.sk_tol - 1e-3) < 1e-9 and p.sk_warm_start == 1
+    assert p.direction == goat.GOAT_DIR_LOT
     assert set(goat.EXPORTED) == set(declared_symbols())
+
+
+def test_direction_is_validated_before_any_device_work(lib_path):
+    # an unknown direction, and FAQ in the batched path, are rejected by the argument
+    # checks; the placeholder pointers are never dereferenced
+    import ctypes
+
+    import numpy as np
+
+    import paper_2111_05366_gb300 as goat
+    lib = goat.load()
+    fake = ctypes.c_void_p(256)
+    perm = np.zeros(8, dtype=np.int32)
+    pp = perm.ctypes.data_as(ctypes.c_void_p)
+    bad = goat.default_params(direction=7)
+    assert lib.goat_match(fake, fake, 8, goat.GOAT_DTYPE_U8, None, ctypes.c_float(0.03), 1, ctypes.c_float(0.03),
+                          ctypes.byref(bad), pp, None, None, None, ctypes.c_size_t(0), None) == goat.GOAT_ERR_INVALID_ARG
+    faq = goat.default_params(direction=goat.GOAT_DIR_LAP)
+    sizes = (ctypes.c_int * 1)(8)
+    offs = (ctypes.c_longlong * 1)(0)
+    assert lib.goat_match_batched(fake, fake, offs, sizes, 1, 1, ctypes.c_ulonglong(0), ctypes.c_float(0.03), 1,
+                                  ctypes.c_float(0.03), ctypes.byref(faq), pp, None, None, None, None, None,
+                                  ctypes.c_size_t(0), None) == goat.GOAT_ERR_INVALID_ARG
 
 
 def test_binding_names_match_abi():
