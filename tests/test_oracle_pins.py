@@ -396,6 +396,37 @@ def test_goat_at_least_faq_on_sbm():
     assert np.mean(acc_g) >= np.mean(acc_f)
 
 
+def test_faq_first_direction_is_the_degree_rearrangement():
+    # at J the gradient is (2/n) d_A d_B^T, so FAQ's first direction maximises
+    # sum_i d_A(i) d_B(pi(i)): by the rearrangement inequality it pairs the vertices
+    # of equal degree rank (unique when the weighted degrees are distinct); the
+    # first step's relaxed iterate then projects back onto that pairing
+    for n, seed in [(60, 1), (150, 8)]:
+        gp = synthetic.rho_er_pair(n, 0.1, 0.8, seed=seed, weighted=True)
+        A, B = gp.A.astype(np.float64), gp.B.astype(np.float64)
+        dA, dB = A.sum(1), B.sum(1)
+        assert np.diff(np.sort(dA)).min() > 0 and np.diff(np.sort(dB)).min() > 0
+        r = oracle.faq(A, B, max_iter=1, tol=1e-4)
+        want = np.empty(n, dtype=np.int32)
+        want[np.argsort(dA)] = np.argsort(dB)
+        np.testing.assert_array_equal(r["perm"], want)
+        assert 0.0 <= r["alphas"][0] < 1.0  # a real step towards the direction (paper's alpha weights P)
+
+
+def test_lot_objective_within_half_percent_of_lap_on_fig1_costs():
+    # Sec. 3.3, Fig. 1: Uniform(100, 150) costs, lambda >= 100; LOT's relaxed
+    # objective <Q, M> stays within 0.5 % of the LAP optimum.  Below it only by the
+    # marginal error of an inexact Q (Birkhoff: the LP attains the LAP optimum).
+    for n, seed in [(100, 1), (250, 2)]:
+        M = synthetic.uniform_costs(n, 100, 150, seed)
+        _, lap_cost = oracle.lap(M, maximize=False)
+        Q, _, _, _, resid = oracle.lot_log(M, 0.01, 1e-3, 20000)
+        assert resid < 1e-3
+        ofv = float((Q * M).sum())
+        assert abs(lap_cost - ofv) / lap_cost < 5e-3
+        assert ofv >= lap_cost * (1 - 2e-3)
+
+
 def test_projection_on_gradient_variant_runs():
     gp = synthetic.rho_er_pair(50, 0.2, 1.0, seed=2)
     r = oracle.goat(gp.A, gp.B, project_on_grad=True)
