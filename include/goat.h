@@ -308,7 +308,8 @@ GOAT_API int goat_objective(const void *A, const void *B, int n, int dtype_AB, c
  *   objective_out, best_restart, fw_iters_out  HOST [num_pairs] (nullable).
  *   relaxed_out  DEVICE float (nullable): the final relaxed P of every problem (the
  *              doubly stochastic "soft matching"), problems in order q, each n x n row-major.
- *   params     precision must be GOAT_PREC_BF16; the Sinkhorn and FW limits apply per problem.
+ *   params     precision must be GOAT_PREC_BF16 and direction GOAT_DIR_LOT (GOAT_ERR_INVALID_ARG
+ *              otherwise); the Sinkhorn and FW limits apply per problem.
  * Workspace: goat_workspace_bytes_batched(n, num_pairs, restarts) bytes, or NULL.
  */
 GOAT_API size_t goat_workspace_bytes_batched(const int *n, int num_pairs, int restarts);
