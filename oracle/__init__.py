@@ -84,6 +84,10 @@ def _load():
                                            ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_int, _ip, _dp, _dp, _ip,
                                            ctypes.POINTER(OracleStats)]),
+            "oracle_goat_seeded": (ctypes.c_int, [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
+                                                  ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip, _dp, _dp, _ip,
+                                                  ctypes.POINTER(OracleStats)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -318,8 +322,12 @@ def brute_qap(A, B, maximize: bool = True):
 
 
 def goat(A, B, P0=None, eps_rel: float = 0.03, max_iter: int = 30, tol: float = 0.03, sk_tol: float = 1e-3,
-         sk_max_iter: int = 500, use_lap: bool = False, maximize: bool = True, project_on_grad: bool = False):
+         sk_max_iter: int = 500, use_lap: bool = False, maximize: bool = True, project_on_grad: bool = False,
+         seeds: int = 0):
     """GOAT (Alg. 3; use_lap=False) or FAQ (Alg. 1; use_lap=True) in FP64.
+
+    seeds = m > 0: seeded graph matching (Fishkind et al., applied in Sec. 4): vertex
+    i of A is known to match vertex i of B for i < m, and only the rest is solved.
 
     Returns a dict with perm, P (final relaxed iterate), alphas (paper's notation),
     sinkhorn_iters, iters, converged, objective."""
@@ -331,10 +339,12 @@ def goat(A, B, P0=None, eps_rel: float = 0.03, max_iter: int = 30, tol: float = 
     alphas = np.zeros(max(max_iter, 1))
     sk = np.zeros(max(max_iter, 1), dtype=np.int32)
     st = OracleStats()
-    _load().oracle_goat(_ptr(A, _dp), _ptr(B, _dp), n, _ptr(P0a, _dp) if P0a is not None else None, eps_rel,
-                        max_iter, tol, sk_tol, sk_max_iter, int(bool(use_lap)), int(bool(maximize)),
-                        int(bool(project_on_grad)), _ptr(perm, _ip), _ptr(P, _dp), _ptr(alphas, _dp),
-                        _ptr(sk, _ip), ctypes.byref(st))
+    if not 0 <= seeds <= n:
+        raise ValueError(f"seeds must lie in [0, {n}]")
+    _load().oracle_goat_seeded(_ptr(A, _dp), _ptr(B, _dp), n, int(seeds),
+                               _ptr(P0a, _dp) if P0a is not None else None, eps_rel, max_iter, tol, sk_tol,
+                               sk_max_iter, int(bool(use_lap)), int(bool(maximize)), int(bool(project_on_grad)),
+                               _ptr(perm, _ip), _ptr(P, _dp), _ptr(alphas, _dp), _ptr(sk, _ip), ctypes.byref(st))
     return {"perm": perm, "P": P, "alphas": alphas[:st.iters], "sinkhorn_iters": sk[:st.iters],
             "iters": st.iters, "converged": bool(st.converged), "objective": st.objective}
 

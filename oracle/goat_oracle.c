@@ -702,45 +702,71 @@ typedef struct {
     double objective;     /* f at the returned permutation                      */
 } oracle_stats;
 
-/* Runs GOAT (use_lap = 0) or FAQ (use_lap = 1) on A, B.
- *   P0            initial doubly stochastic P (NULL: barycenter J = 11^T / n)
- *   eps_rel       entropic weight per iteration: eps = eps_rel * max|grad f(P)|
+/* Runs GOAT (use_lap = 0) or FAQ (use_lap = 1) on A, B, optionally seeded.
+ *   m             seeds: vertex i of A is known to match vertex i of B for i < m
+ *                 (Fishkind et al.'s seeded graph matching, which Sec. 4 applies
+ *                 to both methods).  The iterate keeps the form P = I_m (+) P22,
+ *                 each direction is found on the unseeded block of the gradient
+ *                 (the derivative of f with respect to P22) and padded with I_m,
+ *                 and the final assignment is solved on that block; m = 0 is
+ *                 the unseeded method.
+ *   P0            initial doubly stochastic P (NULL: I_m (+) the barycenter of
+ *                 the unseeded block, 11^T / (n - m)); with seeds it must have the
+ *                 I_m (+) P22 form
+ *   eps_rel       entropic weight per iteration: eps = eps_rel * max|grad f(P)| over
+ *                 the unseeded block
  *   max_iter, tol Frank-Wolfe limits;  sk_tol, sk_max_iter  Sinkhorn limits
  *   maximize      1: graph matching (max f), 0: QAP (min f)
  *   project_on_grad  0: final LAP on P (closest permutation); 1: on grad f(P)
  * Outputs perm (perm[i] = vertex of B matched to vertex i of A), the final
  * relaxed P (nullable), per-iteration step sizes in the paper's notation and
  * Sinkhorn iteration counts (nullable, max_iter entries each). */
-int oracle_goat(const double *A, const double *B, int n, const double *P0, double eps_rel, int max_iter,
-                double tol, double sk_tol, int sk_max_iter, int use_lap, int maximize, int project_on_grad,
-                int *perm, double *P_out, double *alpha_trace, int *sk_iters_trace, oracle_stats *stats)
+int oracle_goat_seeded(const double *A, const double *B, int n, int m, const double *P0, double eps_rel,
+                       int max_iter, double tol, double sk_tol, int sk_max_iter, int use_lap, int maximize,
+                       int project_on_grad, int *perm, double *P_out, double *alpha_trace, int *sk_iters_trace,
+                       oracle_stats *stats)
 {
+    if (m < 0 || m > n) return -1;
     size_t nn = (size_t)n * (size_t)n;
-    double *P = alloc_mat(n), *grad = alloc_mat(n), *M = alloc_mat(n), *Q = alloc_mat(n);
-    int *qperm = (int *)malloc(sizeof(int) * (size_t)n);
-    if (P0) memcpy(P, P0, sizeof(double) * nn);
-    else for (size_t t = 0; t < nn; ++t) P[t] = 1.0 / (double)n;
+    int n2 = n - m; /* unseeded vertices */
+    double *P = alloc_mat(n), *grad = alloc_mat(n), *Q = alloc_mat(n);
+    double *M = alloc_mat(n2 > 0 ? n2 : 1), *Q2 = alloc_mat(n2 > 0 ? n2 : 1);
+    int *qperm = (int *)malloc(sizeof(int) * (size_t)(n2 > 0 ? n2 : 1));
+    if (P0) {
+        memcpy(P, P0, sizeof(double) * nn);
+    } else {
+        for (int i = 0; i < m; ++i) P[IDX(i, i, n)] = 1.0;
+        for (int i = m; i < n; ++i)
+            for (int j = m; j < n; ++j) P[IDX(i, j, n)] = 1.0 / (double)n2;
+    }
 
     int it = 0, converged = 0;
-    while (it < max_iter) {
+    while (n2 > 0 && it < max_iter) {
         /* step 1: gradient */
         oracle_gradient(A, B, P, n, grad);
-        /* step 2: direction.  Maximising tr(Q^T grad) is the rLAP with cost -grad. */
+        /* step 2: direction on the unseeded block.  Maximising tr(Q^T grad) is the
+         * rLAP with cost -grad. */
         double gmax = 0.0;
-        for (size_t t = 0; t < nn; ++t) {
-            M[t] = maximize ? -grad[t] : grad[t];
-            if (fabs(grad[t]) > gmax) gmax = fabs(grad[t]);
-        }
+        for (int i = 0; i < n2; ++i)
+            for (int j = 0; j < n2; ++j) {
+                double v = grad[IDX(m + i, m + j, n)];
+                M[IDX(i, j, n2)] = maximize ? -v : v;
+                if (fabs(v) > gmax) gmax = fabs(v);
+            }
         int sk_it = 0;
         if (use_lap) {
-            oracle_lap_min(M, n, qperm, NULL, NULL);
-            memset(Q, 0, sizeof(double) * nn);
-            for (int i = 0; i < n; ++i) Q[IDX(i, qperm[i], n)] = 1.0;
+            oracle_lap_min(M, n2, qperm, NULL, NULL);
+            memset(Q2, 0, sizeof(double) * (size_t)n2 * (size_t)n2);
+            for (int i = 0; i < n2; ++i) Q2[IDX(i, qperm[i], n2)] = 1.0;
         } else {
             double eps = eps_rel * gmax;
             if (eps <= 0.0) eps = 1.0; /* grad == 0: every doubly stochastic Q is optimal */
-            sk_it = oracle_lot(M, n, eps, sk_tol, sk_max_iter, NULL, Q, NULL, NULL, NULL);
+            sk_it = oracle_lot(M, n2, eps, sk_tol, sk_max_iter, NULL, Q2, NULL, NULL, NULL);
         }
+        memset(Q, 0, sizeof(double) * nn);
+        for (int i = 0; i < m; ++i) Q[IDX(i, i, n)] = 1.0;
+        for (int i = 0; i < n2; ++i)
+            for (int j = 0; j < n2; ++j) Q[IDX(m + i, m + j, n)] = Q2[IDX(i, j, n2)];
         /* step 3: step size (alpha weights P) */
         double alpha = oracle_step_size(A, B, P, Q, n, maximize, NULL, NULL);
         /* step 4: update, and the stopping test on the change of P */
@@ -757,12 +783,18 @@ int oracle_goat(const double *A, const double *B, int n, const double *P0, doubl
         if (sqrt(change) / sqrt((double)n) < tol) { converged = 1; break; }
     }
 
-    /* projection onto the permutations */
-    if (project_on_grad) {
-        oracle_gradient(A, B, P, n, grad);
-        oracle_lap(grad, n, maximize, perm);
-    } else {
-        oracle_lap(P, n, 1, perm);
+    /* projection onto the permutations that keep the seeds */
+    for (int i = 0; i < m; ++i) perm[i] = i;
+    if (n2 > 0) {
+        const double *X = P;
+        if (project_on_grad) {
+            oracle_gradient(A, B, P, n, grad);
+            X = grad;
+        }
+        for (int i = 0; i < n2; ++i)
+            for (int j = 0; j < n2; ++j) M[IDX(i, j, n2)] = X[IDX(m + i, m + j, n)];
+        oracle_lap(M, n2, project_on_grad ? maximize : 1, qperm);
+        for (int i = 0; i < n2; ++i) perm[m + i] = m + qperm[i];
     }
     if (P_out) memcpy(P_out, P, sizeof(double) * nn);
     if (stats) {
@@ -770,6 +802,15 @@ int oracle_goat(const double *A, const double *B, int n, const double *P0, doubl
         stats->converged = converged;
         stats->objective = oracle_objective_perm(A, B, n, perm);
     }
-    free(P); free(grad); free(M); free(Q); free(qperm);
+    free(P); free(grad); free(M); free(Q); free(Q2); free(qperm);
     return 0;
+}
+
+/* The unseeded method (m = 0). */
+int oracle_goat(const double *A, const double *B, int n, const double *P0, double eps_rel, int max_iter,
+                double tol, double sk_tol, int sk_max_iter, int use_lap, int maximize, int project_on_grad,
+                int *perm, double *P_out, double *alpha_trace, int *sk_iters_trace, oracle_stats *stats)
+{
+    return oracle_goat_seeded(A, B, n, 0, P0, eps_rel, max_iter, tol, sk_tol, sk_max_iter, use_lap, maximize,
+                              project_on_grad, perm, P_out, alpha_trace, sk_iters_trace, stats);
 }

@@ -427,6 +427,84 @@ def test_lot_objective_within_half_percent_of_lap_on_fig1_costs():
         assert ofv >= lap_cost * (1 - 2e-3)
 
 
+# --------------------------------------------------------------- seeded matching
+
+def _align_seeds(gp, m):
+    """Relabels B so that vertex i of A matches vertex i of B for i < m; returns (B, truth)."""
+    n = gp.A.shape[0]
+    head = [int(v) for v in gp.truth[:m]]
+    taken = set(head)
+    order = np.array(head + [v for v in range(n) if v not in taken])
+    inv = np.empty(n, dtype=np.int64)
+    inv[order] = np.arange(n)
+    return gp.B[np.ix_(order, order)], inv[gp.truth]
+
+
+def test_seeded_gradient_block_is_the_seeded_objective_gradient():
+    # with P = I_m (+) P22 and symmetric graphs, f = tr(A11 B11) + 2 tr(P22^T A21 B21^T)
+    # + tr(A22 P22 B22 P22^T), whose gradient in P22 is 2 A21 B21^T + 2 A22 P22 B22:
+    # the unseeded block of the full gradient, which the seeded method steps along
+    gp = synthetic.rho_er_pair(40, 0.2, 0.8, seed=4)
+    A, B = gp.A.astype(np.float64), gp.B.astype(np.float64)
+    m = 9
+    P22 = random_ds(40 - m, 3)
+    P = np.zeros((40, 40))
+    P[:m, :m] = np.eye(m)
+    P[m:, m:] = P22
+    want = 2 * A[m:, :m] @ B[m:, :m].T + 2 * A[m:, m:] @ P22 @ B[m:, m:]
+    np.testing.assert_allclose(oracle.gradient(A, B, P)[m:, m:], want, rtol=1e-12, atol=1e-12)
+    f_blocks = (np.trace(A[:m, :m] @ B[:m, :m]) + 2 * np.sum(P22 * (A[m:, :m] @ B[m:, :m].T))
+                + np.trace(A[m:, m:] @ P22 @ B[m:, m:] @ P22.T))
+    assert oracle.objective(A, B, P) == pytest.approx(f_blocks, rel=1e-12)
+
+
+def test_seeds_are_kept_and_full_seeding_is_the_identity():
+    gp = synthetic.rho_er_pair(30, 0.2, 0.7, seed=5)
+    for m in (0, 1, 12, 29, 30):
+        for lap in (False, True):
+            r = oracle.goat(gp.A, gp.B, seeds=m, use_lap=lap)
+            np.testing.assert_array_equal(r["perm"][:m], np.arange(m))
+            assert sorted(r["perm"]) == list(range(30))
+            if m >= 29:  # at most one free vertex: nothing to solve
+                np.testing.assert_array_equal(r["perm"], np.arange(30))
+    assert oracle.goat(gp.A, gp.B, seeds=30)["iters"] == 0
+
+
+def test_seeded_small_pairs_against_brute_force():
+    # the seeded result never beats the best seed-respecting permutation, and reaches
+    # it on isomorphic pairs
+    n, m = 7, 3
+    for seed in range(4):
+        gp = synthetic.rho_er_pair(n, 0.5, 1.0, seed=seed)
+        B, truth = _align_seeds(gp, m)
+        A64, B64 = gp.A.astype(np.float64), B.astype(np.float64)
+        best = max(oracle.objective_perm(A64, B64, np.array(list(range(m)) + [m + q for q in rest]))
+                   for rest in itertools.permutations(range(n - m)))
+        assert oracle.objective_perm(A64, B64, truth) == best
+        for lap in (False, True):
+            r = oracle.goat(A64, B64, seeds=m, use_lap=lap)
+            assert r["objective"] <= best + 1e-9
+        assert oracle.goat(A64, B64, seeds=m)["objective"] == best
+
+
+def test_seeds_recover_sbm_pairs():
+    # Sec. 4 (seeded experiment, after Fishkind et al.): on rho-SBM pairs with the
+    # paper's block matrix, a few seeds turn a failed unseeded match into an exact one
+    # (rho = 0.6), and GOAT matches at least as many vertices as FAQ with seeds (rho = 0.3)
+    Pb = [[0.7, 0.3, 0.4], [0.3, 0.7, 0.3], [0.4, 0.3, 0.7]]
+    acc = {}
+    for rho, m in ((0.6, 0), (0.6, 10), (0.3, 30)):
+        g, f = [], []
+        for seed in range(2):
+            gp = synthetic.rho_sbm_pair([40, 40, 40], Pb, rho, seed=seed)
+            B, truth = _align_seeds(gp, m)
+            g.append((oracle.goat(gp.A, B, seeds=m)["perm"] == truth).mean())
+            f.append((oracle.faq(gp.A, B, seeds=m)["perm"] == truth).mean())
+        acc[rho, m] = (np.mean(g), np.mean(f))
+    assert acc[0.6, 0][0] < 0.1 and acc[0.6, 10][0] == 1.0
+    assert acc[0.3, 30][0] >= acc[0.3, 30][1]
+
+
 def test_projection_on_gradient_variant_runs():
     gp = synthetic.rho_er_pair(50, 0.2, 1.0, seed=2)
     r = oracle.goat(gp.A, gp.B, project_on_grad=True)
