@@ -1,0 +1,54 @@
+"""Host-side helpers of bench.py that feed its JSON line (no GPU): the peak
+denominators and the per-launch DRAM traffic read from the committed ncu summaries."""
+import hashlib
+import importlib.util
+import os
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_host_module", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_measured_peaks_are_read_when_present():
+    bench = _bench()
+    p = bench.measured_peaks()
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        assert p["source"] == "measured"
+    else:
+        assert p["source"] == "fallback" and p["hbm_gbs"] == 6800.0
+    assert p["bf16_tflops_sustained"] > 0
+
+
+def test_committed_8bit_traffic_matches_the_current_product_kernel():
+    # the timed form's roofline.traffic comes from this capture; a change to the
+    # product kernel makes it stale (bench.py then reports null) until it is re-taken
+    bench = _bench()
+    t = bench.gemm_traffic_per_launch(32768, "k_gemm_xyT_fp8_traffic.txt")
+    assert t == pytest.approx(36.695e9), "k_gemm_xyT changed since profiles/k_gemm_xyT_fp8_traffic.txt was captured"
+
+
+def test_traffic_is_dropped_when_the_kernel_source_changes(tmp_path):
+    bench = _bench()
+    root = tmp_path / "repo"
+    (root / "profiles").mkdir(parents=True)
+    (root / "paper_2111_05366_gb300" / "csrc").mkdir(parents=True)
+    src = root / "paper_2111_05366_gb300" / "csrc" / "goat_gemm.cu"
+    src.write_bytes(b"// kernel v1\n")
+    digest = hashlib.sha256(b"// kernel v1\n").hexdigest()
+    (root / "profiles" / "t.txt").write_text(f"# capture\nn: 1000\ndram_bytes_per_launch: 5e9\nsource_sha256: {digest}\n")
+    bench.ROOT = str(root)
+    assert bench.gemm_traffic_per_launch(1000, "t.txt") == 5e9
+    # scaled to another size by the n^3 growth of the operand re-reads
+    assert bench.gemm_traffic_per_launch(2000, "t.txt") == pytest.approx(40e9)
+    src.write_bytes(b"// kernel v2\n")
+    assert bench.gemm_traffic_per_launch(1000, "t.txt") is None
+    assert bench.gemm_traffic_per_launch(1000, "missing.txt") is None
+    shutil.rmtree(root)
