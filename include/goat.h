@@ -324,22 +324,29 @@ GOAT_API int goat_match_batched(const void *A, const void *B, const long long *a
  * The paper has no counterpart: this exists for callers that must not allocate
  * device memory during the call (they run under an allocator they do not own,
  * inside a fixed memory budget, or on a thread that must not synchronise with the
- * device the way cudaMalloc/cudaFree can).  It allocates nothing and never waits
- * on the device: its scratch is one static device array of about 2 MiB, held by
- * every GPU that loads the library until the process exits.
+ * device the way cudaMalloc/cudaFree can).  It allocates nothing and never
+ * synchronises with the device: its scratch is one static device array of about
+ * 2 MiB, held by every GPU that loads the library until the process exits.
  *   G, n, eps, tol, f_out, g_io  as in goat_sinkhorn; n <= 4096, larger n returns
  *                                 GOAT_ERR_INVALID_ARG (the array is sized for 4096).
- *   max_iter   iteration slots queued; once the residual falls below tol the
- *              remaining slots do no work, so the result equals goat_sinkhorn's.
- *   iters_out, resid_out  DEVICE int / float (nullable), written when the stream
- *              reaches the end of the call.
+ *   max_iter   iteration slots queued, 1 <= max_iter <= 1000 (GOAT_ERR_INVALID_ARG
+ *              otherwise); once the residual falls below tol the remaining slots do
+ *              no work, so the result equals goat_sinkhorn's.  Every slot is about
+ *              five kernel launches, so a long queue can make the host block inside
+ *              the launch calls until the GPU drains it (launch-queue back-pressure).
+ *   iters_out, resid_out, status_out  DEVICE int / float / int (nullable), written
+ *              when the stream reaches the end of the call.  *status_out is GOAT_OK
+ *              or GOAT_ERR_NAN (a non-finite residual, e.g. from a non-finite G):
+ *              the return value only reports errors found before the launches.
  * The first call on each device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All calls
- * share the one array and each starts by clearing its state block, so calls
- * that overlap on the GPU (other streams, other host threads) race: serialise them.
+ * device current); make that first call before any stream capture.  The lookup is
+ * repeated only when the device's context has changed (after cudaDeviceReset).
+ * All calls share the one array and each starts by clearing its state block, so
+ * calls that overlap on the GPU (other streams, other host threads) race: serialise them.
  */
 GOAT_API int goat_sinkhorn_noalloc(const float *G, int n, float eps, float tol, int max_iter, float *f_out,
-                                   float *g_io, int *iters_out, float *resid_out, goat_stream_t stream);
+                                   float *g_io, int *iters_out, float *resid_out, int *status_out,
+                                   goat_stream_t stream);
 
 /*
  * Learned Sinkhorn warm start.  The paper has no counterpart; it serves Alg. 2:

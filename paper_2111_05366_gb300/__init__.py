@@ -125,7 +125,7 @@ def load():
             "goat_objective": (_i, [_vp, _vp, _i, _i, _vp, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp,
                                     ctypes.c_size_t, _vp]),
             "goat_gemm_bf16_xyT": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _i, _f, _vp, _i, _i, _i, _vp]),
-            "goat_sinkhorn_noalloc": (_i, [_vp, _i, _f, _f, _i, _vp, _vp, _vp, _vp, _vp]),
+            "goat_sinkhorn_noalloc": (_i, [_vp, _i, _f, _f, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
             "goat_workspace_bytes_batched": (ctypes.c_size_t, [_vp, _i, _i]),
             "goat_dual_features": (_i, [_vp, _vp, _vp, _i, _i, _f, _vp, _vp, ctypes.c_size_t, _vp]),
             "goat_mlp_forward": (_i, [_vp, _vp, _i, _vp, _vp]),
@@ -396,30 +396,35 @@ def goat_gemm_bf16_xyT(X, Y, k_total: int, kx_period: int, scale: float = 1.0, o
 
 
 NOALLOC_MAX_N = 4096
+NOALLOC_MAX_ITER = 1000
 
 
 def goat_sinkhorn_noalloc(G, eps: float, tol: float, max_iter: int, g_init=None):
     """goat_sinkhorn for callers that cannot allocate device memory during the call.
 
-    The library side allocates nothing and does not wait on the device; this
-    wrapper creates the output tensors itself for convenience (a caller that
-    cannot allocate passes preallocated f, g, iters, resid through the C ABI).
-    n <= NOALLOC_MAX_N.  Returns (f, g, iters, resid) with iters/resid as
-    one-element device tensors."""
+    The library side allocates nothing and does not synchronise with the device;
+    this wrapper creates the output tensors itself for convenience (a caller that
+    cannot allocate passes preallocated f, g, iters, resid, status through the C
+    ABI).  n <= NOALLOC_MAX_N, max_iter <= NOALLOC_MAX_ITER.  Returns
+    (f, g, iters, resid, status) with iters / resid / status as one-element
+    device tensors (status: GOAT_OK or GOAT_ERR_NAN)."""
     torch = _torch()
     n = G.shape[0]
     if n > NOALLOC_MAX_N:
         raise ValueError(f"n = {n} exceeds the no-allocation maximum of {NOALLOC_MAX_N}")
+    if max_iter > NOALLOC_MAX_ITER:
+        raise ValueError(f"max_iter = {max_iter} exceeds the no-allocation maximum of {NOALLOC_MAX_ITER}")
     f = torch.empty(n, dtype=torch.float32, device=G.device)
     g = (g_init.clone() if g_init is not None else torch.zeros(n, dtype=torch.float32, device=G.device))
     it = torch.zeros(1, dtype=torch.int32, device=G.device)
     res = torch.zeros(1, dtype=torch.float32, device=G.device)
+    status = torch.zeros(1, dtype=torch.int32, device=G.device)
     r = load().goat_sinkhorn_noalloc(_dev(G, torch.float32, (n, n), "G"), n, float(eps), float(tol), int(max_iter),
                                      _dev(f, torch.float32, (n,), "f"), _dev(g, torch.float32, (n,), "g"),
                                      _dev(it, torch.int32, (1,), "iters"), _dev(res, torch.float32, (1,), "resid"),
-                                     _stream())
+                                     _dev(status, torch.int32, (1,), "status"), _stream())
     _check(r, "goat_sinkhorn_noalloc")
-    return f, g, it, res
+    return f, g, it, res, status
 
 
 BATCH_MAX_N = 2048

@@ -21,7 +21,7 @@ namespace goat {
 enum : int { NEED_GEMM = 1, NEED_FW = 2, NEED_SK = 4, NEED_LAP = 8, NEED_HOSTCOPY = 16 };
 
 struct Plan {
-    size_t state, A16, B16, Xq, C1, GQ, P, G, f, g, deg, partial, lap, perm, Ad, Bd, Id, cost, mlp, total;
+    size_t state, A16, B16, Xq, C1, GQ, P, G, f, g, deg, partial, lap, perm, Ad, Bd, Id, cost, objpart, mlp, rearr, total;
     size_t A8, B8, Q8, C8, f8s;  // E4M3 operands and their scales (8-bit form)
     int ld, terms, ld8;
     bool fp8;
@@ -43,6 +43,7 @@ static Plan make_plan(int n, int dtype, int precision, int need) {
     w.fp8 = precision == GOAT_PREC_FP8;
     w.state = take(sizeof(DevState));
     w.cost = take(16 * sizeof(double));  // [0,3) u64 sums, [3,6) f64 sums, [6] assignment cost, [7,10) LAP bound
+    w.objpart = take(3 * kObjBlocks * sizeof(double));  // per-block partials of the FP64 objective sums
     if (need & (NEED_GEMM | NEED_FW)) {
         w.A16 = take((size_t)n * w.ld * 2);
         w.B16 = take((size_t)n * w.ld * 2);
@@ -64,6 +65,7 @@ static Plan make_plan(int n, int dtype, int precision, int need) {
         w.g = take((size_t)n * 4);
         w.deg = take((size_t)2 * n * 4);
         w.mlp = take(mlp_warm_start_scratch_bytes(n));
+        w.rearr = take(rearrangement_scratch_bytes(n));
     }
     if (need & (NEED_SK | NEED_FW)) {
         const size_t sk = (size_t)sinkhorn_partial_elems(n) * 8;
@@ -347,11 +349,17 @@ static int match_impl(const void *A, const void *B, int n, int dtype, const floa
         if (faq) {
             // FAQ (Alg. 1): Q = argmax over permutations of <Pi, grad f(P)> = argmin <Pi, G>;
             // an uncertified assignment is still a permutation, so it is used
-            LapReport drep{};
-            double dgap = 0.0;
-            const int dst = lap_solve(G, n, 0, perm_dev, ws.at<void>(w.lap), st, ctl, ws.at<double>(w.cost) + 6,
-                                      pinned, &dgap, &drep, s);
-            if (dst != GOAT_OK && dst != GOAT_ERR_NOT_CONVERGED) return dst;
+            if (it == 0 && !init) {
+                // at the barycenter grad f(J) is rank one: the assignment is the
+                // rearrangement pairing of the degrees, solved exactly
+                GOAT_TRY(rearrangement_perm(A, B, dtype, n, ws.at<void>(w.rearr), perm_dev, s));
+            } else {
+                LapReport drep{};
+                double dgap = 0.0;
+                const int dst = lap_solve(G, n, 0, perm_dev, ws.at<void>(w.lap), st, ctl,
+                                          ws.at<double>(w.cost) + 6, pinned, &dgap, &drep, s);
+                if (dst != GOAT_OK && dst != GOAT_ERR_NOT_CONVERGED) return dst;
+            }
             if (prof) cudaEventRecord(pe[1], s);
             GOAT_TRY(write_perm_q(perm_dev, n, Xq, w.ld, w.terms, s));
         } else {
@@ -438,7 +446,7 @@ static int match_impl(const void *A, const void *B, int n, int dtype, const floa
     double *fsums = ws.at<double>(w.cost) + 3;
     GOAT_TRY(cuda_status(cudaMemsetAsync(isums, 0, 6 * sizeof(double), s)));
     GOAT_TRY(objective(A, B, dtype, n, perm_dev, isums, fsums, isums + 1, isums + 2, fsums + 1, fsums + 2,
-                       &st->bad_perm, s));
+                       &st->bad_perm, ws.at<double>(w.objpart), s));
     unsigned long long hi[3];
     double hf[3];
     GOAT_TRY(cuda_status(cudaMemcpyAsync(hi, isums, sizeof(hi), cudaMemcpyDeviceToHost, s)));
@@ -750,7 +758,7 @@ int goat_objective(const void *A, const void *B, int n, int dtype_AB, const int3
     double *fsums = ws.at<double>(w.cost) + 3;
     GOAT_TRY(cuda_status(cudaMemsetAsync(isums, 0, 6 * sizeof(double), s)));
     GOAT_TRY(objective(A, B, dtype_AB, n, perm, isums, fsums, isums + 1, isums + 2, fsums + 1, fsums + 2,
-                       &st->bad_perm, s));
+                       &st->bad_perm, ws.at<double>(w.objpart), s));
     unsigned long long hi[3];
     double hf[3];
     int bad = 0;

@@ -414,14 +414,85 @@ __global__ void k_fw_roll(DevState *st) {
     st->gmax_next = 0u;
 }
 
+// ---------------------------------------------------------------- FAQ's first direction
+
+// FAQ (Alg. 1) started at the barycenter: the direction step solves the linear
+// assignment max_perm sum_i grad f(J)[i][perm i] with grad f(J) = (2/n) d_A d_B^T
+// (symmetric A, B).  The matrix is rank one, so by the rearrangement inequality
+// the optimum pairs the k-th largest degree of A with the k-th largest of B.
+// Solving the assignment on the FP32 matrix instead is not exact: two pairings
+// that swap vertices of nearly equal degree differ by about (relative degree
+// gap)^2 of an entry, below FP32's resolution of G.  The degrees here are FP64
+// sums (exact for 0/1 and for weights with few significant bits); equal degrees
+// are ordered by vertex index, and every such order is an optimum.
+
+// deg[i] = sum_j A[i][j] in FP64; one warp per row, a fixed lane order and tree.
+template <typename T>
+__global__ void __launch_bounds__(256) k_degrees_f64(const T *__restrict__ A, int n, double *__restrict__ deg) {
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb) {
+        const T *row = A + (long long)i * n;
+        double acc = 0.0;
+        for (int j = lane; j < n; j += 32) acc += (double)row[j];
+        acc = warp_sum_d(acc);
+        if (lane == 0) deg[i] = acc;
+    }
+}
+
+// rank[i] = #{k : d_k > d_i, or d_k = d_i and k < i} (0 = largest), for two degree
+// vectors at once (blockIdx.y selects A or B); the degrees pass through shared
+// memory in tiles of 256.
+__global__ void __launch_bounds__(256) k_degree_rank(const double *__restrict__ deg, int n, int *__restrict__ rank) {
+    __shared__ double tile[256];
+    const double *d = deg + (long long)blockIdx.y * n;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double di = i < n ? d[i] : 0.0;
+    int r = 0;
+    for (int k0 = 0; k0 < n; k0 += 256) {
+        __syncthreads();
+        if (k0 + (int)threadIdx.x < n) tile[threadIdx.x] = d[k0 + threadIdx.x];
+        __syncthreads();
+        const int lim = min(256, n - k0);
+        for (int t = 0; t < lim; ++t) {
+            const double dk = tile[t];
+            r += (dk > di) || (dk == di && k0 + t < i);
+        }
+    }
+    if (i < n) rank[(long long)blockIdx.y * n + i] = r;
+}
+
+// inv[rank_B[j]] = j; then perm[i] = inv[rank_A[i]].
+__global__ void k_rank_invert(const int *__restrict__ rankB, int n, int *__restrict__ inv) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) inv[rankB[j]] = j;
+}
+__global__ void k_rank_pair(const int *__restrict__ rankA, const int *__restrict__ inv, int n, int32_t *perm) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) perm[i] = inv[rankA[i]];
+}
+
 // ---------------------------------------------------------------- objective
 
-// sum_ij A_ij B[perm i][perm j]; exact 64-bit integer sums for byte inputs,
-// FP64 for float inputs.  One block per row range.
+// Block-wide FP64 sum in a fixed order (a warp tree, then the warps in order);
+// the result is valid in thread 0.  Every thread of the block calls it.
+__device__ __forceinline__ double block_sum_fixed(double v) {
+    __shared__ double s_part[32];
+    v = warp_sum_d(v);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_part[w];
+    __syncthreads();
+    return t;
+}
+
+// sum_ij A_ij B[perm i][perm j]: exact 64-bit integer sums for byte inputs; for
+// float inputs FP64 sums, one partial per block (fixed grid kObjBlocks) added in
+// block order by k_sum_in_order, so the value is the same on every run.  Block b
+// takes the rows b, b + gridDim.x, ...
 template <typename T>
 __global__ void __launch_bounds__(256) k_objective(const T *__restrict__ A, const T *__restrict__ B,
                                                    const int32_t *__restrict__ perm, int n,
-                                                   unsigned long long *isum, double *fsum, int *bad_perm) {
+                                                   unsigned long long *isum, double *fpart, int *bad_perm) {
     long long acc_i = 0;
     double acc_f = 0.0;
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
@@ -445,22 +516,19 @@ __global__ void __launch_bounds__(256) k_objective(const T *__restrict__ A, cons
             }
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        acc_i += __shfl_xor_sync(0xffffffffu, acc_i, o);
-        acc_f += __shfl_xor_sync(0xffffffffu, acc_f, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (sizeof(T) == 1)
-            atomicAdd(isum, (unsigned long long)acc_i);
-        else
-            atomicAdd(fsum, acc_f);
+    if (sizeof(T) == 1) {
+        for (int o = 16; o > 0; o >>= 1) acc_i += __shfl_xor_sync(0xffffffffu, acc_i, o);
+        if ((threadIdx.x & 31) == 0 && acc_i) atomicAdd(isum, (unsigned long long)acc_i);  // exact in any order
+    } else {
+        const double t = block_sum_fixed(acc_f);
+        if (threadIdx.x == 0) fpart[blockIdx.x] = t;
     }
 }
 
-// Sum of squared entries (||A||_F^2) for the disagreement count.
+// Sum of squared entries (||A||_F^2) for the disagreement count; same scheme.
 template <typename T>
 __global__ void __launch_bounds__(256) k_sqnorm(const T *__restrict__ A, long long total, unsigned long long *isum,
-                                                double *fsum) {
+                                                double *fpart) {
     long long ai = 0;
     double af = 0.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -471,16 +539,22 @@ __global__ void __launch_bounds__(256) k_sqnorm(const T *__restrict__ A, long lo
         else
             af += (double)a * (double)a;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        ai += __shfl_xor_sync(0xffffffffu, ai, o);
-        af += __shfl_xor_sync(0xffffffffu, af, o);
+    if (sizeof(T) == 1) {
+        for (int o = 16; o > 0; o >>= 1) ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        if ((threadIdx.x & 31) == 0 && ai) atomicAdd(isum, (unsigned long long)ai);
+    } else {
+        const double t = block_sum_fixed(af);
+        if (threadIdx.x == 0) fpart[blockIdx.x] = t;
     }
-    if ((threadIdx.x & 31) == 0) {
-        if (sizeof(T) == 1)
-            atomicAdd(isum, (unsigned long long)ai);
-        else
-            atomicAdd(fsum, af);
-    }
+}
+
+// out[k] = sum_b part[k * count + b] over b in increasing order, k < sets; one thread per set.
+__global__ void k_sum_in_order(const double *__restrict__ part, int count, int sets, double *out) {
+    const int k = threadIdx.x;
+    if (k >= sets) return;
+    double t = 0.0;
+    for (int b = 0; b < count; ++b) t += part[(long long)k * count + b];
+    out[k] = t;
 }
 
 // ---------------------------------------------------------------- host wrappers
@@ -555,6 +629,28 @@ void absmax(const float *X, long long total, unsigned *out, cudaStream_t s) {
     k_absmax<<<grid_for(total), 256, 0, s>>>(X, total, out);
 }
 
+size_t rearrangement_scratch_bytes(int n) { return (size_t)n * (2 * sizeof(double) + 3 * sizeof(int)); }
+
+int rearrangement_perm(const void *A, const void *B, int dtype, int n, void *scratch, int32_t *perm, cudaStream_t s) {
+    double *deg = reinterpret_cast<double *>(scratch);
+    int *rank = reinterpret_cast<int *>(deg + 2 * (size_t)n);
+    int *inv = rank + 2 * (size_t)n;
+    const int gw = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 8), 152LL * 16));
+    if (dtype == GOAT_DTYPE_U8) {
+        k_degrees_f64<uint8_t><<<gw, 256, 0, s>>>((const uint8_t *)A, n, deg);
+        k_degrees_f64<uint8_t><<<gw, 256, 0, s>>>((const uint8_t *)B, n, deg + n);
+    } else {
+        k_degrees_f64<float><<<gw, 256, 0, s>>>((const float *)A, n, deg);
+        k_degrees_f64<float><<<gw, 256, 0, s>>>((const float *)B, n, deg + n);
+    }
+    k_degree_rank<<<dim3((unsigned)ceil_div(n, 256), 2), 256, 0, s>>>(deg, n, rank);
+    const int g = (int)std::min<int64_t>(ceil_div(n, 256), 1024);
+    k_rank_invert<<<g, 256, 0, s>>>(rank + n, n, inv);
+    k_rank_pair<<<g, 256, 0, s>>>(rank, inv, n, perm);
+    note_launches(5);
+    return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
+}
+
 // FAQ's direction (Alg. 1): Q = the permutation matrix of perm (Q[i][perm i] = 1),
 // as BF16 terms in the GEMM operand buffer, which the caller zeroed.
 __global__ void __launch_bounds__(256) k_write_perm_q(const int32_t *__restrict__ perm, int n,
@@ -593,19 +689,23 @@ void fw_roll(DevState *st, cudaStream_t s) { k_fw_roll<<<1, 1, 0, s>>>(st); }
 
 int objective(const void *A, const void *B, int dtype, int n, const int32_t *perm, unsigned long long *isum,
               double *fsum, unsigned long long *nA, unsigned long long *nB, double *fA, double *fB, int *bad,
-              cudaStream_t s) {
-    note_launches(3);
-    note_launches(1);
-    const int grid = (int)std::min<long long>(n, 152LL * 8);
+              double *fpart, cudaStream_t s) {
     const long long total = (long long)n * n;
     if (dtype == GOAT_DTYPE_U8) {
-        k_objective<uint8_t><<<grid, 256, 0, s>>>((const uint8_t *)A, (const uint8_t *)B, perm, n, isum, fsum, bad);
-        k_sqnorm<uint8_t><<<grid_for(total), 256, 0, s>>>((const uint8_t *)A, total, nA, fA);
-        k_sqnorm<uint8_t><<<grid_for(total), 256, 0, s>>>((const uint8_t *)B, total, nB, fB);
+        note_launches(3);
+        const int grid = (int)std::min<long long>(n, 152LL * 8);
+        k_objective<uint8_t><<<grid, 256, 0, s>>>((const uint8_t *)A, (const uint8_t *)B, perm, n, isum, nullptr, bad);
+        k_sqnorm<uint8_t><<<grid_for(total), 256, 0, s>>>((const uint8_t *)A, total, nA, nullptr);
+        k_sqnorm<uint8_t><<<grid_for(total), 256, 0, s>>>((const uint8_t *)B, total, nB, nullptr);
     } else {
-        k_objective<float><<<grid, 256, 0, s>>>((const float *)A, (const float *)B, perm, n, isum, fsum, bad);
-        k_sqnorm<float><<<grid_for(total), 256, 0, s>>>((const float *)A, total, nA, fA);
-        k_sqnorm<float><<<grid_for(total), 256, 0, s>>>((const float *)B, total, nB, fB);
+        // fixed grids: the FP64 partial sums and their order do not depend on the device
+        note_launches(4);
+        k_objective<float><<<kObjBlocks, 256, 0, s>>>((const float *)A, (const float *)B, perm, n, isum, fpart, bad);
+        k_sqnorm<float><<<kObjBlocks, 256, 0, s>>>((const float *)A, total, nA, fpart + kObjBlocks);
+        k_sqnorm<float><<<kObjBlocks, 256, 0, s>>>((const float *)B, total, nB, fpart + 2 * kObjBlocks);
+        // fsum, fA, fB are consecutive doubles (the callers' layout)
+        if (fA != fsum + 1 || fB != fsum + 2) return GOAT_ERR_INVALID_ARG;
+        k_sum_in_order<<<1, 32, 0, s>>>(fpart, kObjBlocks, 3, fsum);
     }
     return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
 }

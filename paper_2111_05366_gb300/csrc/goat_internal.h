@@ -77,26 +77,6 @@ int gemm_grouped(const GemmGroupCall &c, cudaStream_t stream);
 void note_launches(int k);
 long long launches_so_far();
 
-// Byte layout of the scratch workspace for size n (all offsets 256-aligned).
-struct Workspace {
-    size_t state;       // DevState
-    size_t A16, B16;    // BF16 adjacency, n rows x ld
-    size_t Xq;          // BF16 split terms of the right operand (Q or P), n rows x (terms*ld)
-    size_t C1;          // BF16 split terms of (Q B)^T, n rows x (terms*ld)
-    size_t GQ;          // FP32 n x n  (-grad f(Q))
-    size_t P, G;        // FP32 n x n  (goat_match's own iterate and -gradient)
-    size_t Qf;          // FP32 n x n  scratch (unused by goat_match)
-    size_t f, g;        // FP32 duals
-    size_t deg;         // FP32 degrees of A and B (2n)
-    size_t partial;     // FP32 Sinkhorn column partial sums / FP64 reduction partials
-    size_t lap;         // auction scratch
-    size_t total;
-    int ld, terms;
-    long long partial_elems;
-};
-
-Workspace plan_workspace(int n, int dtype_AB, int precision, bool with_match_buffers);
-
 struct DevState;
 
 // goat_fw.cu
@@ -114,9 +94,13 @@ void line_search(const float *G, const float *GQ, const float *P, const __nv_bfl
 void fw_update(float *P, float *G, const float *GQ, const __nv_bfloat16 *Qb, int ldq, int terms, const float *Qf,
                int n, const DevState *st, float alpha_value, unsigned *gmax_out, cudaStream_t s);
 void fw_roll(DevState *st, cudaStream_t s);
+// Blocks of the FP64 objective sums (a fixed grid, so the sums are reproducible);
+// objective() takes 3 * kObjBlocks doubles of scratch in fpart, and fsum, fA, fB
+// must be consecutive doubles.
+constexpr int kObjBlocks = 512;
 int objective(const void *A, const void *B, int dtype, int n, const int32_t *perm, unsigned long long *isum,
               double *fsum, unsigned long long *nA, unsigned long long *nB, double *fA, double *fB, int *bad,
-              cudaStream_t s);
+              double *fpart, cudaStream_t s);
 
 // goat_sinkhorn.cu
 long long sinkhorn_partial_elems(int n);
@@ -125,6 +109,11 @@ int sinkhorn_solve(const float *G, int n, long long ld, float *f, float *g, doub
                    int max_iter, int check_every, int *host_flag, cudaStream_t s);
 void sinkhorn_queue_fixed(const float *G, int n, long long ld, float *f, float *g, double *partial, DevState *st,
                           int max_iter, cudaStream_t s);
+// FAQ's first direction at the barycenter, exactly: perm pairs the k-th largest FP64
+// degree of A with the k-th largest of B (grad f(J) is rank one).  scratch holds
+// rearrangement_scratch_bytes(n) bytes (8-byte aligned).
+size_t rearrangement_scratch_bytes(int n);
+int rearrangement_perm(const void *A, const void *B, int dtype, int n, void *scratch, int32_t *perm, cudaStream_t s);
 // Zeroes the operand buffer and writes the permutation matrix of perm into it (FAQ's Q).
 int write_perm_q(const int32_t *perm, int n, __nv_bfloat16 *Qb, int ldq, int terms, cudaStream_t s);
 void write_q(const float *G, int n, long long ld, const float *f, const float *g, const DevState *st,

@@ -215,6 +215,10 @@ __global__ void k_lap_reset(int n, const LapBuffers L, DevState *st, int reset_p
 }
 
 // Appends the rows of the `want` lanes to a bidder list (one atomic per warp).
+// The order of a list is run-dependent and does not matter: a Jacobi round's
+// outcome depends only on the set of bidders (each object goes to its highest
+// bid, the lowest row among equal bids), and the augmenting-path searches relax
+// over their lists with ties broken by row index.
 __device__ __forceinline__ void list_append(bool want, int row, int *dst, int *count) {
     const unsigned m = __ballot_sync(0xffffffffu, want);
     if (!m) return;
@@ -307,6 +311,33 @@ __global__ void k_lap_assign(const LapBuffers L, DevState *st, int cur) {
     }
 }
 
+// Appends the unassigned rows to queue[*s_tail ...] in increasing row order (a
+// block-wide ordered compaction: warp ballots, then the warps' counts in order),
+// so that the sequential bidding below visits the rows in the same order on every
+// run.  The order decides which of several tied optima the auction settles on.
+// Every thread of the block calls it; s_cnt holds 32 ints of shared memory.
+__device__ __forceinline__ void queue_free_rows_in_order(const int *__restrict__ assign, int n,
+                                                         int *__restrict__ queue, int *s_tail, int *s_cnt) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + tid;
+        const bool fr = i < n && assign[i] < 0;
+        const unsigned m = __ballot_sync(0xffffffffu, fr);
+        if (lane == 0) s_cnt[warp] = __popc(m);
+        __syncthreads();
+        int off = *s_tail;
+        for (int w = 0; w < warp; ++w) off += s_cnt[w];
+        if (fr) queue[off + __popc(m & ((1u << lane) - 1u))] = i;
+        __syncthreads();
+        if (tid == 0) {
+            int add = 0;
+            for (int w = 0; w < nwarps; ++w) add += s_cnt[w];
+            *s_tail += add;
+        }
+        __syncthreads();
+    }
+}
+
 // Gauss-Seidel tail of a phase: one CTA serves the unassigned rows one at a
 // time; a bid takes its object at once and the evicted holder joins the queue
 // (a ring of n slots: a row is queued only while unassigned).  All threads scan
@@ -318,6 +349,7 @@ __global__ void __launch_bounds__(1024) k_lap_tail(const float *__restrict__ M, 
     __shared__ i64 s_b1[32], s_b2[32];
     __shared__ int s_j1[32];
     __shared__ int s_head, s_tail, s_stop;
+    __shared__ int s_cnt[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     if (tid == 0) {
         s_head = 0;
@@ -325,9 +357,7 @@ __global__ void __launch_bounds__(1024) k_lap_tail(const float *__restrict__ M, 
         s_stop = 0;
     }
     __syncthreads();
-    for (int i = tid; i < n; i += blockDim.x)
-        if (L.assign[i] < 0) L.queue[atomicAdd(&s_tail, 1)] = i;
-    __syncthreads();
+    queue_free_rows_in_order(L.assign, n, L.queue, &s_tail, s_cnt);
     long long bids = 0, since = 0;
     int qmin = s_tail - s_head;
     while (true) {
@@ -423,24 +453,8 @@ __global__ void __cluster_dims__(LAP_CLUSTER, 1, 1) __launch_bounds__(256)
             s_bids = 0;
         }
         __syncthreads();
-        for (int base = 0; base < n; base += blockDim.x) {  // queue the unassigned rows in row order
-            const int i = base + tid;
-            const bool fr = i < n && L.assign[i] < 0;
-            const unsigned m = __ballot_sync(0xffffffffu, fr);
-            __shared__ int s_cnt[8];
-            if (lane == 0) s_cnt[warp] = __popc(m);
-            __syncthreads();
-            int off = s_tail;
-            for (int w = 0; w < warp; ++w) off += s_cnt[w];
-            if (fr) L.queue[off + __popc(m & ((1u << lane) - 1u))] = i;
-            __syncthreads();
-            if (tid == 0) {
-                int add = 0;
-                for (int w = 0; w < nwarps; ++w) add += s_cnt[w];
-                s_tail += add;
-            }
-            __syncthreads();
-        }
+        __shared__ int s_cnt[32];
+        queue_free_rows_in_order(L.assign, n, L.queue, &s_tail, s_cnt);
         if (tid == 0) {
             s_qmin = s_tail - s_head;
             s_since = 0;
@@ -563,7 +577,8 @@ __global__ void __cluster_dims__(LAP_CLUSTER, 1, 1) __launch_bounds__(256)
 // Slack of every assigned row, delta_i = max_j (a_ij - p_j) - (a_i,j_i - p_j_i) >= 0,
 // into my_bid[i], and its object into my_obj[i] (the pairs whose benefit a~ adds
 // delta_i); every unassigned row gets the potential u_i = -max_j (a_ij - p_j) in
-// ufree[i] and is listed in queue[0, lap_free).  One CTA per row.
+// ufree[i] and is listed in queue[0, lap_free) (in a run-dependent order, which the
+// searches do not depend on: see list_append).  One CTA per row.
 __global__ void __launch_bounds__(256) k_lap_sap_prep(const float *__restrict__ M, int n, const Quant q,
                                                       const LapBuffers L, DevState *st) {
     __shared__ i64 s_b1[8], s_b2[8];
@@ -1093,13 +1108,12 @@ __global__ void __launch_bounds__(1024) k_lap_fill(const float *__restrict__ M, 
     if (tid == 0) st->lap_unassigned = 0;
 }
 
-// Duality gap of the quantised problem, sum_i (max_j (a_ij - p_j) - (a_i,perm i - p_perm i)),
-// each term >= 0, accumulated into *out as a double.  One warp per row.
+// Duality gap of the quantised problem, sum_i (max_j (a_ij - p_j) - (a_i,perm i - p_perm i)):
+// each row's term (>= 0) into term[i], one warp per row; k_lap_gap_sum adds them.
 __global__ void __launch_bounds__(256) k_lap_gap(const float *__restrict__ M, int n, const Quant q,
-                                                 const LapBuffers L, double *out) {
+                                                 const LapBuffers L, i64 *__restrict__ term) {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    double acc = 0.0;
     for (int i = gw; i < n; i += nw) {
         i64 b1 = kNegInf, b2 = kNegInf;
         int j1 = INT_MAX;
@@ -1108,10 +1122,26 @@ __global__ void __launch_bounds__(256) k_lap_gap(const float *__restrict__ M, in
         top2_warp(b1, b2, j1);
         if (lane == 0) {
             const int j = L.assign[i];
-            if (j >= 0 && j < n) acc += (double)(b1 - (benefit(Mi[j], q) - L.price[j]));
+            term[i] = (j >= 0 && j < n) ? b1 - (benefit(Mi[j], q) - L.price[j]) : 0;
         }
     }
-    if (lane == 0 && acc != 0.0) atomicAdd(out, acc);
+}
+
+// *out = sum_i term[i] as a double, in a fixed order (thread t adds rows t, t + 1024,
+// ... in turn, then the threads' sums are combined by a fixed tree): the same value
+// on every run.  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_lap_gap_sum(const i64 *__restrict__ term, int n, double *out) {
+    __shared__ double s[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += (double)term[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+        *out = t;
+    }
 }
 
 // sum_i M[i][perm i] in FP64 in row order (the order the oracle uses); one block.
@@ -1312,9 +1342,9 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
     note_launches(1);
     // duality gap in quantised units; below Qm it proves the assignment optimal
     double *gap_dev = cost_dev + 1;
-    cudaMemsetAsync(gap_dev, 0, sizeof(double), s);
-    k_lap_gap<<<gbid, 256, 0, s>>>(M, n, q, L, gap_dev);
-    note_launches(1);
+    k_lap_gap<<<gbid, 256, 0, s>>>(M, n, q, L, L.ufree);  // the free rows' potentials are no longer needed
+    k_lap_gap_sum<<<1, 1024, 0, s>>>(L.ufree, n, gap_dev);
+    note_launches(2);
     double gq = 0.0;
     long long counts[3] = {0, 0, 0};
     cudaMemcpyAsync(&gq, gap_dev, sizeof(double), cudaMemcpyDeviceToHost, s);

@@ -7,7 +7,7 @@
 // that has no way to hand us a workspace.  goat_sinkhorn_noalloc serves them: its
 // scratch (the device state block and the column partial sums) lives in one
 // file-scope device array that every GPU loading the library holds until exit,
-// and it neither allocates nor waits on the device.
+// and it neither allocates nor synchronises with the device.
 #include <cstring>
 #include <mutex>
 
@@ -18,6 +18,8 @@ namespace goat {
 
 // Largest n this entry point accepts; the scratch below is sized for it.
 constexpr int kNoallocMaxN = 4096;
+// Largest max_iter: every iteration slot is queued up front (about five launches each).
+constexpr int kNoallocMaxIter = 1000;
 // DevState (rounded to 16 KiB) + at most ceil(n / 64) row chunks x n FP64 column partials.
 constexpr size_t kNoallocStateBytes = 16384;
 constexpr size_t kNoallocScratchBytes = kNoallocStateBytes + (size_t)(kNoallocMaxN / 64) * kNoallocMaxN * 8;
@@ -26,11 +28,40 @@ static_assert(sizeof(DevState) <= kNoallocStateBytes, "state block does not fit 
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-// Address of g_noalloc_scratch on each device, looked up once per device with
-// that device current (the host-side symbol is a stand-in, not a device address).
+// Identity of the calling thread's current CUDA context (0 if none or unknown),
+// through the driver's cuCtxGetCurrent / cuCtxGetId entry points.
+static unsigned long long current_context_id() {
+    typedef int (*get_current_fn)(void **);
+    typedef int (*get_id_fn)(void *, unsigned long long *);
+    static get_current_fn get_current = nullptr;
+    static get_id_fn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<get_current_fn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<get_id_fn>(p);
+        cudaGetLastError();
+    });
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of g_noalloc_scratch in the current context (the host-side symbol
+// is a stand-in, not a device address).  Looked up once per device, with that
+// device current, and again only if the device's context has changed since (after
+// a cudaDeviceReset the array lives at a new address).
 static unsigned char *noalloc_scratch_address(int *status) {
     static std::mutex mu;
     static unsigned char *addr[64] = {};
+    static unsigned long long ctx_of[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
         cudaGetLastError();
@@ -38,7 +69,8 @@ static unsigned char *noalloc_scratch_address(int *status) {
         return nullptr;
     }
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!addr[dev] || ctx == 0 || ctx != ctx_of[dev]) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
@@ -47,6 +79,7 @@ static unsigned char *noalloc_scratch_address(int *status) {
             return nullptr;
         }
         addr[dev] = static_cast<unsigned char *>(p);
+        ctx_of[dev] = current_context_id();  // the lookup above makes the primary context current
     }
     *status = GOAT_OK;
     return addr[dev];
@@ -59,9 +92,10 @@ __global__ void k_noalloc_state_init(DevState *st) {
     st->c = 1.4426950408889634f;
 }
 
-__global__ void k_noalloc_report(const DevState *st, int *iters_out, float *resid_out) {
+__global__ void k_noalloc_report(const DevState *st, int *iters_out, float *resid_out, int *status_out) {
     if (iters_out) *iters_out = st->sk_iters;
     if (resid_out) *resid_out = st->sk_resid;
+    if (status_out) *status_out = st->error;
 }
 
 }  // namespace goat
@@ -71,10 +105,11 @@ using namespace goat;
 extern "C" {
 
 int goat_sinkhorn_noalloc(const float *G, int n, float eps, float tol, int max_iter, float *f_out, float *g_io,
-                          int *iters_out, float *resid_out, goat_stream_t stream) {
+                          int *iters_out, float *resid_out, int *status_out, goat_stream_t stream) {
     if (!G || !f_out || !g_io || n < 1 || !(eps > 0.0f) || !(tol >= 0.0f) || max_iter < 1)
         return GOAT_ERR_INVALID_ARG;
-    if (n > kNoallocMaxN) return GOAT_ERR_INVALID_ARG;  // beyond the static scratch
+    if (n > kNoallocMaxN) return GOAT_ERR_INVALID_ARG;            // beyond the static scratch
+    if (max_iter > kNoallocMaxIter) return GOAT_ERR_INVALID_ARG;  // bounded launch queue
     int dev = 0, major = 0, minor = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
@@ -99,7 +134,7 @@ int goat_sinkhorn_noalloc(const float *G, int n, float eps, float tol, int max_i
     note_launches(1);
     sinkhorn_begin(st, eps, tol, nullptr, n, s);
     sinkhorn_queue_fixed(G, n, n, f_out, g_io, partial, st, max_iter, s);
-    k_noalloc_report<<<1, 1, 0, s>>>(st, iters_out, resid_out);
+    k_noalloc_report<<<1, 1, 0, s>>>(st, iters_out, resid_out, status_out);
     note_launches(1);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;

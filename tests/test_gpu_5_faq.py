@@ -4,13 +4,13 @@ loop with the Hungarian method as the direction step).
 
 FAQ's directions are argmax problems with ties on 0/1 graphs (Sec. 3.1), and a
 tie settled differently sends the two runs apart.  The parity cases therefore use
-weighted graphs (lognormal weights), whose directions are unique: the first
-step, where grad f(J) is rank one and the assignment is the sorting of weighted
-degrees, and isomorphic pairs, which FAQ solves in two steps.  The seeds are ones
-whose weighted degrees are all distinct (no tie in the first assignment).  The
-weights are drawn representable in BF16, the format the products take adjacency
-values in, so that the FP32 form computes the gradient exactly and the step sizes
-agree with the FP64 oracle to rounding."""
+weighted graphs (lognormal weights), whose directions are unique once the
+weighted degrees are distinct: the first step, where grad f(J) = (2/n) d_A d_B^T
+is rank one and the assignment is the rearrangement pairing of the degrees (the
+library solves it exactly from FP64 degrees), and isomorphic pairs, which FAQ
+solves in a few steps.  The weights are drawn representable in BF16, the format
+the products take adjacency values in, so that the FP32 form computes the
+gradient exactly and the step sizes agree with the FP64 oracle to rounding."""
 import numpy as np
 import pytest
 
@@ -38,14 +38,17 @@ def _faq_gpu(A, B, precision, **kw):
     return goat.goat_match(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), params=prm, **kw)
 
 
-@pytest.mark.parametrize("n,seed", [(60, 1), (150, 8), (150, 4)])
+def _distinct_degrees(A, B):
+    dA, dB = A.astype(np.float64).sum(1), B.astype(np.float64).sum(1)
+    return np.unique(dA).size == dA.size and np.unique(dB).size == dB.size
+
+
+@pytest.mark.parametrize("n,seed", [(60, 1), (150, 8), (150, 4), (300, 9)])
 def test_faq_first_step_matches_oracle(n, seed):
-    # grad f(J) = (2/n) d_A d_B^T is rank one: two assignments that swap vertices of
-    # close weighted degree differ by about (relative degree gap)^2 of an entry,
-    # below the resolution of the FP32 gradient the assignment is solved on, so the
-    # direction is checked for optimality to that resolution, and the step for the
-    # direction taken against the oracle's exact line search
+    # distinct weighted degrees: the first assignment is unique, and the GPU's must be
+    # the oracle Hungarian's, exactly; the step size must be the oracle's for it
     A, B, _ = _weighted_pair(n, 0.8, seed)
+    assert _distinct_degrees(A, B)
     perm, obj, st = _faq_gpu(A, B, goat.GOAT_PREC_FP32, max_iter=1, tol=1e-4)
     assert st["fw_iters"] == 1 and st["sk_iters"][0] == 0
     A64, B64 = A.astype(np.float64), B.astype(np.float64)
@@ -53,9 +56,8 @@ def test_faq_first_step_matches_oracle(n, seed):
     grad = oracle.gradient(A64, B64, J)
     # alpha > 0, so P = (1 - alpha) J + alpha Pi projects onto the direction Pi itself
     assert st["alpha"][0] > 0
-    _, best = oracle.lap(grad, maximize=True)
-    mine = float(grad[np.arange(n), perm].sum())
-    assert mine >= best - n * float(np.abs(grad).max()) * 2.0 ** -23, (mine, best)
+    ref, _ = oracle.lap(grad, maximize=True)
+    np.testing.assert_array_equal(perm, ref)
     Pi = np.zeros((n, n))
     Pi[np.arange(n), perm] = 1.0
     alpha_paper, _, _ = oracle.step_size(A64, B64, J, Pi)
@@ -64,18 +66,43 @@ def test_faq_first_step_matches_oracle(n, seed):
     assert obj == pytest.approx(oracle.objective_perm(A64, B64, perm), rel=1e-9)
 
 
-@pytest.mark.parametrize("n,seed", [(100, 5), (300, 9)])
+def test_faq_first_step_with_tied_degrees_is_an_optimum():
+    # two vertices of equal weighted degree: several first assignments are optimal
+    # (Sec. 3.1's ties); the GPU's must reach the Hungarian optimum's value
+    A, B, _ = _weighted_pair(300, 1.0, 6)
+    assert not _distinct_degrees(A, B)
+    perm, _, st = _faq_gpu(A, B, goat.GOAT_PREC_FP32, max_iter=1, tol=1e-4)
+    grad = oracle.gradient(A.astype(np.float64), B.astype(np.float64), np.full((300, 300), 1.0 / 300))
+    _, best = oracle.lap(grad, maximize=True)
+    mine = float(grad[np.arange(300), perm].sum())
+    assert mine == pytest.approx(best, rel=1e-12)
+
+
+@pytest.mark.parametrize("n,seed", [(100, 5), (300, 9), (300, 2)])
 def test_faq_recovers_weighted_isomorphic_pairs(n, seed):
     A, B, truth = _weighted_pair(n, 1.0, seed)
+    assert _distinct_degrees(A, B)
     perm, obj, st = _faq_gpu(A, B, goat.GOAT_PREC_FP32, max_iter=30, tol=1e-4)
     ro = oracle.faq(A.astype(np.float64), B.astype(np.float64), max_iter=30, tol=1e-4)
     assert (ro["perm"] == truth).all()
     np.testing.assert_array_equal(perm, truth)
     assert st["converged"] and ro["converged"]
-    # a first direction that differs from the oracle's only below FP32 resolution
-    # (see above) costs at most a step or two more
-    assert st["fw_iters"] <= ro["iters"] + 2
+    # the same directions as the oracle's, hence the same number of steps and step sizes
+    assert st["fw_iters"] == ro["iters"]
+    np.testing.assert_allclose(st["alpha"], 1.0 - np.asarray(ro["alphas"]), atol=1e-5)
     assert obj == pytest.approx(ro["objective"], rel=1e-6)
+
+
+def test_faq_is_deterministic_on_tied_inputs():
+    # 0/1 graphs: many tied assignments at every step; two runs must return the same
+    # permutation, the same step sizes and the same number of steps
+    gp = synthetic.rho_er_pair(400, 0.05, 0.7, seed=21)
+    runs = [_faq_gpu(gp.A, gp.B, goat.GOAT_PREC_BF16, max_iter=15, tol=1e-4) for _ in range(3)]
+    for perm, obj, st in runs[1:]:
+        np.testing.assert_array_equal(perm, runs[0][0])
+        assert obj == runs[0][1]
+        assert st["fw_iters"] == runs[0][2]["fw_iters"]
+        assert st["alpha"] == runs[0][2]["alpha"]
 
 
 @pytest.mark.parametrize("precision", [goat.GOAT_PREC_FP8, goat.GOAT_PREC_BF16, goat.GOAT_PREC_FP32])
