@@ -12,7 +12,7 @@
  * Conventions shared by every entry point
  *   - Matrices are dense, row-major, leading dimension n, in DEVICE memory
  *     unless the name ends in _host.  Vectors likewise.
- *   - A and B are symmetric with a zero diagonal (simple undirected graphs).
+ *   - A and B are symmetric (undirected graphs) unless a call says otherwise.
  *     With that, grad f(P) = A P B^T + A^T P B = 2 A P B.
  *   - G denotes MINUS the gradient, G = -grad f(P) (so G <= 0 for
  *     non-negative graphs); the direction step solves min_Q <Q, G> - eps H(Q).
@@ -120,6 +120,23 @@ typedef struct goat_params {
      * auction cannot certify within its budget is still a permutation and is used.
      * goat_match_batched takes GOAT_DIR_LOT only. */
     int direction;
+    /* 1 (default): graph matching, maximise f (Sec. 2.2); 0: QAP, minimise f (eq. QAP).
+     * Minimising runs the same iteration on G = +grad f. */
+    int maximize;
+    /* Seeded matching (Sec. 4's seeded experiment): vertex i of A is known to match
+     * vertex i of B for i < seeds (0 <= seeds <= n).  The iterate keeps the form
+     * I_seeds (+) P22; gradient, direction, step and projection run on the unseeded
+     * block, the seeds entering as a constant term of its gradient; eps, the stop
+     * test (with the full n) and the returned permutation follow the unseeded method.
+     * init, if given, must have the I_seeds (+) P22 form (only its block is read). */
+    int seeds;
+    /* 0 (default): A and B must be symmetric (checked; GOAT_ERR_INVALID_ARG
+     * otherwise), grad f = 2 A P B (two products).  1: general (directed or
+     * asymmetric weighted) graphs, grad f = A P B^T + A^T P B (four products). */
+    int directed;
+    /* DEVICE n x n float (nullable): receives the final relaxed iterate P, the
+     * doubly stochastic soft matching (I_seeds (+) P22 with seeds). */
+    float *relaxed_out;
 } goat_params;
 
 typedef struct goat_stats {
@@ -161,10 +178,16 @@ GOAT_API size_t goat_workspace_bytes(int n, int dtype_AB, int precision);
  * copies of A, B and init).  Returns 0 for n < 1. */
 GOAT_API size_t goat_workspace_bytes_host(int n, int dtype_AB, int precision);
 
+/* Bytes of scratch goat_match (host = 0) or goat_match_host (host = 1) needs with
+ * goat_params.directed = directed and goat_params.seeds = seeds (the two calls
+ * above are directed = 0, seeds = 0).  Returns 0 for invalid arguments. */
+GOAT_API size_t goat_workspace_bytes_ex(int n, int dtype_AB, int precision, int directed, int seeds, int host);
+
 /*
  * goat_match -- the whole GOAT solve (Alg. 3), or FAQ (Alg. 1) with
- * p->direction = GOAT_DIR_LAP.
- *   A, B       device, n x n, dtype_AB, symmetric, zero diagonal (checked:
+ * p->direction = GOAT_DIR_LAP; QAP minimisation, seeded matching and directed
+ * graphs through p->maximize, p->seeds and p->directed.
+ *   A, B       device, n x n, dtype_AB; symmetric unless p->directed = 1 (checked:
  *              GOAT_ERR_INVALID_ARG otherwise).
  *   init       device n x n float doubly stochastic start, or NULL for the
  *              barycenter J = 11^T / n (Alg. 3 "Initialize").
@@ -194,6 +217,17 @@ GOAT_API int goat_match_host(const void *A_host, const void *B_host, int n, int 
  */
 GOAT_API int goat_gradient(const void *A, const void *B, int n, int dtype_AB, const float *P, float *G_out, int precision,
                   void *workspace, size_t workspace_bytes, goat_stream_t stream);
+
+/*
+ * goat_gradient_ex -- goat_gradient for general graphs (Alg. 1 / Alg. 3 step 1 with
+ * no symmetry): with directed = 1, G_out = -(A P B^T + A^T P B) by four products
+ * (C1 = B P^T, C1' = B^T P^T, then [A | A^T] [C1 | C1']^T in one accumulation);
+ * directed = 0 is goat_gradient.  Workspace: goat_workspace_bytes_ex(n, dtype_AB,
+ * precision, directed, 0, 0) bytes, or NULL.
+ */
+GOAT_API int goat_gradient_ex(const void *A, const void *B, int n, int dtype_AB, const float *P, float *G_out,
+                              int precision, int directed, void *workspace, size_t workspace_bytes,
+                              goat_stream_t stream);
 
 /*
  * goat_sinkhorn -- LOT (Alg. 2): entropic rLAP min_Q <Q, G> - eps H(Q) over doubly

@@ -39,8 +39,8 @@ GOAT_TRACE_MAX = 256
 GOAT_MLP_PARAMS = 641
 
 EXPORTED = ["goat_default_params", "goat_strerror", "goat_workspace_bytes", "goat_workspace_bytes_host",
-            "goat_match", "goat_match_host",
-            "goat_gradient", "goat_sinkhorn", "goat_line_search", "goat_fw_update", "goat_project",
+            "goat_workspace_bytes_ex", "goat_match", "goat_match_host",
+            "goat_gradient", "goat_gradient_ex", "goat_sinkhorn", "goat_line_search", "goat_fw_update", "goat_project",
             "goat_objective", "goat_gemm_bf16_xyT", "goat_sinkhorn_noalloc", "goat_match_batched",
             "goat_workspace_bytes_batched", "goat_dual_features", "goat_mlp_forward", "goat_mlp_train_step",
             "goat_mlp_warm_start", "goat_lap_default_options", "goat_project_ex"]
@@ -56,7 +56,8 @@ class goat_params(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("sk_max_iter", ctypes.c_int), ("sk_tol", ctypes.c_float),
                 ("sk_warm_start", ctypes.c_int), ("sk_check_every", ctypes.c_int),
                 ("project_on_grad", ctypes.c_int), ("lap_max_rounds", ctypes.c_int), ("profile", ctypes.c_int),
-                ("mlp_weights", ctypes.c_void_p), ("direction", ctypes.c_int)]
+                ("mlp_weights", ctypes.c_void_p), ("direction", ctypes.c_int), ("maximize", ctypes.c_int),
+                ("seeds", ctypes.c_int), ("directed", ctypes.c_int), ("relaxed_out", ctypes.c_void_p)]
 
 
 class goat_stats(ctypes.Structure):
@@ -107,11 +108,13 @@ def load():
             "goat_strerror": (ctypes.c_char_p, [_i]),
             "goat_workspace_bytes": (ctypes.c_size_t, [_i, _i, _i]),
             "goat_workspace_bytes_host": (ctypes.c_size_t, [_i, _i, _i]),
+            "goat_workspace_bytes_ex": (ctypes.c_size_t, [_i, _i, _i, _i, _i, _i]),
             "goat_match": (_i, [_vp, _vp, _i, _i, _vp, _f, _i, _f, ctypes.POINTER(goat_params), _vp,
                                 ctypes.POINTER(_d), ctypes.POINTER(goat_stats), _vp, ctypes.c_size_t, _vp]),
             "goat_match_host": (_i, [_vp, _vp, _i, _i, _vp, _f, _i, _f, ctypes.POINTER(goat_params), _vp,
                                      ctypes.POINTER(_d), ctypes.POINTER(goat_stats), _vp, ctypes.c_size_t, _vp]),
             "goat_gradient": (_i, [_vp, _vp, _i, _i, _vp, _vp, _i, _vp, ctypes.c_size_t, _vp]),
+            "goat_gradient_ex": (_i, [_vp, _vp, _i, _i, _vp, _vp, _i, _i, _vp, ctypes.c_size_t, _vp]),
             "goat_sinkhorn": (_i, [_vp, _i, _f, _f, _i, _vp, _vp, _vp, ctypes.POINTER(_i), ctypes.POINTER(_f), _vp,
                                    ctypes.c_size_t, _vp]),
             "goat_line_search": (_i, [_vp, _vp, _vp, _vp, _i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d),
@@ -195,15 +198,17 @@ def default_params(**overrides) -> goat_params:
             raise KeyError(k)
         if k == "mlp_weights" and v is not None and not isinstance(v, int):
             v = _dev(v, _torch().bfloat16, (GOAT_MLP_PARAMS,), "mlp_weights").value
+        if k == "relaxed_out" and v is not None and not isinstance(v, int):
+            v = _dev(v, _torch().float32, None, "relaxed_out").value
         setattr(p, k, v)
     return p
 
 
 def workspace_bytes(n: int, dtype_AB: int = GOAT_DTYPE_U8, precision: int = GOAT_PREC_BF16,
-                    host: bool = False) -> int:
+                    host: bool = False, directed: int = 0, seeds: int = 0) -> int:
     """Scratch bytes goat_match (host=False) or goat_match_host (host=True) needs for size n."""
-    fn = load().goat_workspace_bytes_host if host else load().goat_workspace_bytes
-    return int(fn(int(n), int(dtype_AB), int(precision)))
+    return int(load().goat_workspace_bytes_ex(int(n), int(dtype_AB), int(precision), int(directed), int(seeds),
+                                              int(bool(host))))
 
 
 def _stats_dict(st: goat_stats) -> dict:
@@ -273,14 +278,15 @@ def goat_match_host(A, B, init=None, eps_rel: float = 0.03, max_iter: int = 30, 
     return perm, obj.value, _stats_dict(st)
 
 
-def goat_gradient(A, B, P, precision: int = GOAT_PREC_BF16, out=None):
-    """G = -grad f(P) = -2 A P B (Alg. 3 step 1) on the tensor cores; returns a float32 tensor."""
+def goat_gradient(A, B, P, precision: int = GOAT_PREC_BF16, out=None, directed: bool = False):
+    """G = -grad f(P) (Alg. 3 step 1) on the tensor cores: -2 A P B for symmetric graphs,
+    -(A P B^T + A^T P B) with directed=True.  Returns a float32 tensor."""
     torch = _torch()
     n = A.shape[0]
     G = out if out is not None else torch.empty((n, n), dtype=torch.float32, device=A.device)
-    r = load().goat_gradient(_dev(A, A.dtype, (n, n), "A"), _dev(B, A.dtype, (n, n), "B"), n, _adj_dtype(A),
-                             _dev(P, torch.float32, (n, n), "P"), _dev(G, torch.float32, (n, n), "G"),
-                             int(precision), None, 0, _stream())
+    r = load().goat_gradient_ex(_dev(A, A.dtype, (n, n), "A"), _dev(B, A.dtype, (n, n), "B"), n, _adj_dtype(A),
+                                _dev(P, torch.float32, (n, n), "P"), _dev(G, torch.float32, (n, n), "G"),
+                                int(precision), int(bool(directed)), None, 0, _stream())
     _check(r, "goat_gradient")
     return G
 

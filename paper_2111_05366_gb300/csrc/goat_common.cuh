@@ -35,6 +35,7 @@ struct DevState {
     int fw_iter;
     int maximize;
     float fw_tol;
+    int stop_n;           // n of the stop test's ||P_new - P||_F / sqrt(n) (0: the solved size)
     int error;            // first device-side error (goat_status), 0 if none
     double ls_a, ls_b, ls_dd, alpha;
     int lap_unassigned;   // auction: bidders without an object

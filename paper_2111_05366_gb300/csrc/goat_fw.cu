@@ -12,18 +12,20 @@ namespace goat {
 
 // ---------------------------------------------------------------- operands
 
-// Adjacency (uint8 or float32, dense ld n) -> BF16 GEMM operand (row stride ld16,
-// zero padding), plus row sums (degrees) in FP32.  One warp per row.
+// A rows x cols window of an adjacency matrix (uint8 or float32, leading dimension
+// lda) -> BF16 GEMM operand rows of `width` elements (zero beyond cols), `stride`
+// elements apart, plus the window's row sums in FP32 (deg, nullable).  One warp per row.
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_to_bf16(const T *__restrict__ A, int n, __nv_bfloat16 *__restrict__ A16,
-                                                     int ld16, float *__restrict__ deg) {
+__global__ void __launch_bounds__(256) k_adj_to_bf16(const T *__restrict__ A, long long lda, int rows, int cols,
+                                                     __nv_bfloat16 *__restrict__ A16, int width, long long stride,
+                                                     float *__restrict__ deg) {
     const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb) {
-        const T *src = A + (long long)i * n;
-        __nv_bfloat16 *dst = A16 + (long long)i * ld16;
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < rows; i += gridDim.x * wpb) {
+        const T *src = A + (long long)i * lda;
+        __nv_bfloat16 *dst = A16 + (long long)i * stride;
         float s = 0.0f;
-        for (int j = lane; j < ld16; j += 32) {
-            const float v = (j < n) ? (float)src[j] : 0.0f;
+        for (int j = lane; j < width; j += 32) {
+            const float v = (j < cols) ? (float)src[j] : 0.0f;
             dst[j] = __float2bfloat16_rn(v);
             s += v;
         }
@@ -39,19 +41,59 @@ __device__ __forceinline__ unsigned short e4m3x2(float a, float b) {
     return (unsigned short)__nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
 }
 
-// Adjacency (uint8 or float32, dense ld n) -> E4M3 GEMM operand, row stride ld8,
-// zero padding.  0/1 entries are exact (1.0 = 0x38); other weights round to E4M3.
+// The same window -> E4M3 GEMM operand rows (`width` bytes, even, zero beyond
+// cols, `stride` bytes apart).  0/1 entries are exact (1.0 = 0x38); other weights
+// round to E4M3.
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_to_e4m3(const T *__restrict__ A, int n, uint8_t *__restrict__ A8,
-                                                     int ld8) {
-    const int pairs = ld8 / 2;
-    const long long total = (long long)n * pairs;
+__global__ void __launch_bounds__(256) k_adj_to_e4m3(const T *__restrict__ A, long long lda, int rows, int cols,
+                                                     uint8_t *__restrict__ A8, int width, long long stride) {
+    const int pairs = width / 2;
+    const long long total = (long long)rows * pairs;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(t / pairs), j = (int)(t - (long long)i * pairs) * 2;
-        const T *src = A + (long long)i * n;
-        const float a = j < n ? (float)src[j] : 0.0f, b = j + 1 < n ? (float)src[j + 1] : 0.0f;
-        *reinterpret_cast<unsigned short *>(A8 + (long long)i * ld8 + j) = e4m3x2(a, b);
+        const T *src = A + (long long)i * lda;
+        const float a = j < cols ? (float)src[j] : 0.0f, b = j + 1 < cols ? (float)src[j + 1] : 0.0f;
+        *reinterpret_cast<unsigned short *>(A8 + (long long)i * stride + j) = e4m3x2(a, b);
+    }
+}
+
+// The transpose of a rows x cols window -> operand rows (dst row c = source column
+// c): dst[c][r] = A[r][c] for r < rows, zero for rows <= r < width; dst rows
+// 0..cols-1, `stride` elements apart.  32 x 32 tiles through shared memory; grid
+// (ceil(width / 32), ceil(cols / 32)), block 32 x 8.  O is __nv_bfloat16 or uint8_t (E4M3).
+template <typename T, typename O>
+__global__ void k_adj_transpose(const T *__restrict__ A, long long lda, int rows, int cols, O *__restrict__ dst,
+                                int width, long long stride) {
+    __shared__ float tile[32][33];
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int k = ty; k < 32; k += 8) {
+        const int r = r0 + k, c = c0 + tx;
+        tile[k][tx] = (r < rows && c < cols) ? (float)A[(long long)r * lda + c] : 0.0f;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int c = c0 + k, r = r0 + tx;
+        if (c < cols && r < width) {
+            const float v = tile[tx][k];
+            if constexpr (sizeof(O) == 1)
+                dst[(long long)c * stride + r] = (O)(e4m3x2(v, 0.0f) & 0xFFu);
+            else
+                dst[(long long)c * stride + r] = __float2bfloat16_rn(v);
+        }
+    }
+}
+
+// Column sums of a rows x cols window in FP32 (the in-degrees of a directed graph);
+// one thread per column, the rows in order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_col_sums(const T *__restrict__ A, long long lda, int rows, int cols,
+                                                  float *__restrict__ out) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int r = 0; r < rows; ++r) s += (float)A[(long long)r * lda + c];
+        out[c] = s;
     }
 }
 
@@ -109,7 +151,7 @@ __global__ void __launch_bounds__(256) k_bf16_to_e4m3(const __nv_bfloat16 *__res
     }
 }
 
-// Counts pairs with A[i][j] != A[j][i] (32 x 32 tiles through shared memory).
+// Counts entries with A[i][j] != A[j][i] (32 x 32 tiles through shared memory).
 template <typename T>
 __global__ void k_count_asym(const T *__restrict__ A, int n, int *__restrict__ count) {
     __shared__ float tile[32][33];
@@ -127,7 +169,6 @@ __global__ void k_count_asym(const T *__restrict__ A, int n, int *__restrict__ c
         if (i < n && j < n) {
             const float a = (float)A[(long long)i * n + j];
             if (a != tile[tx][r]) ++bad;
-            if (i == j && a != 0.0f) ++bad;  // diagonal must be zero
         }
     }
     if (bad) atomicAdd(count, bad);
@@ -163,18 +204,28 @@ __global__ void __launch_bounds__(256) k_f32_to_terms(const float *__restrict__ 
 // ---------------------------------------------------------------- first gradient
 
 // At the barycenter J = 11^T/n:  grad f(J) = (A 1)(B 1)^T / n + (A^T 1)(B^T 1)^T / n,
-// i.e. G = -(2/n) d_A d_B^T for symmetric graphs.  Also fills P = J and records max|G|.
-__global__ void __launch_bounds__(256) k_barycenter(const float *__restrict__ dA, const float *__restrict__ dB, int n,
-                                                    float *__restrict__ G, float *__restrict__ P, DevState *st) {
+// the out-degrees d_A, d_B and in-degrees e_A, e_B, so
+//   G = scale (d_A d_B^T + e_A e_B^T) [+ C]
+// with scale = -sigma / n (sigma = +1 to maximise f, -1 to minimise it); for
+// symmetric graphs e = d and the kernel is called with scale = -2 sigma / n and no
+// in-degrees.  C (nullable) is a constant term of the gradient (the seeds' share),
+// P (nullable) is set to J.  max|G| goes to st->gmax_bits.
+__global__ void __launch_bounds__(256) k_barycenter(const float *__restrict__ dA, const float *__restrict__ dB,
+                                                    const float *__restrict__ eA, const float *__restrict__ eB, int n,
+                                                    float scale, const float *__restrict__ C, float *__restrict__ G,
+                                                    float *__restrict__ P, DevState *st) {
     const float inv_n = 1.0f / (float)n;
-    const float scale = -2.0f * inv_n;
     float gm = 0.0f;
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
         const float ai = scale * dA[i];
+        const float bi = eA ? scale * eA[i] : 0.0f;
         float *Gi = G + (long long)i * n;
         float *Pi = P ? P + (long long)i * n : nullptr;
+        const float *Ci = C ? C + (long long)i * n : nullptr;
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const float v = ai * dB[j];
+            float v = ai * dB[j];
+            if (eA) v = fmaf(bi, eB[j], v);
+            if (Ci) v += Ci[j];
             Gi[j] = v;
             if (Pi) Pi[j] = inv_n;
             gm = fmaxf(gm, fabsf(v));
@@ -182,6 +233,49 @@ __global__ void __launch_bounds__(256) k_barycenter(const float *__restrict__ dA
     }
     gm = warp_max(gm);
     if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&st->gmax_bits, gm);
+}
+
+// X += C elementwise (the seeds' constant share of every gradient): float4 at a time
+// over the first total - total % 4 elements (both 16-byte aligned), then the tail.
+__global__ void __launch_bounds__(256) k_add_f32(float *__restrict__ X, const float *__restrict__ C, long long total) {
+    const long long total4 = total >> 2;
+    float4 *x4 = reinterpret_cast<float4 *>(X);
+    const float4 *c4 = reinterpret_cast<const float4 *>(C);
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = tid; t < total4; t += stride) {
+        float4 a = x4[t];
+        const float4 b = __ldg(c4 + t);
+        a.x += b.x;
+        a.y += b.y;
+        a.z += b.z;
+        a.w += b.w;
+        x4[t] = a;
+    }
+    for (long long t = (total4 << 2) + tid; t < total; t += stride) X[t] += C[t];
+}
+
+// Seeded matching: the block solution perm[m..n) (indices into the unseeded block)
+// becomes the full permutation, and the seeds map to themselves.
+__global__ void k_seed_perm(int32_t *perm, int n, int m) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        perm[i] = i < m ? i : perm[i] + m;
+}
+
+// out (n_full x n_full) = I_m (+) P22, P22 the n x n block iterate (n = n_full - m).
+__global__ void __launch_bounds__(256) k_embed_block(const float *__restrict__ P22, int n, int m,
+                                                     float *__restrict__ out) {
+    const int nf = n + m;
+    for (int i = blockIdx.x; i < nf; i += gridDim.x) {
+        float *row = out + (long long)i * nf;
+        for (int j = threadIdx.x; j < nf; j += blockDim.x) {
+            float v;
+            if (i < m || j < m)
+                v = (i == j) ? 1.0f : 0.0f;
+            else
+                v = P22[(long long)(i - m) * n + (j - m)];
+            row[j] = v;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(256) k_absmax(const float *__restrict__ X, long long total, unsigned *out) {
@@ -336,7 +430,7 @@ __global__ void k_ls_final(const double *__restrict__ part, int nblocks, int n, 
     st->ls_b = b;
     st->ls_dd = s3;
     st->alpha = alpha;
-    const double change = alpha * sqrt(s3 > 0.0 ? s3 : 0.0) / sqrt((double)n);
+    const double change = alpha * sqrt(s3 > 0.0 ? s3 : 0.0) / sqrt((double)(st->stop_n > 0 ? st->stop_n : n));
     const int it = st->fw_iter;
     if (it < GOAT_TRACE_MAX) {
         st->tr_alpha[it] = alpha;
@@ -441,16 +535,20 @@ __global__ void __launch_bounds__(256) k_degrees_f64(const T *__restrict__ A, in
 
 // rank[i] = #{k : d_k > d_i, or d_k = d_i and k < i} (0 = largest), for two degree
 // vectors at once (blockIdx.y selects A or B); the degrees pass through shared
-// memory in tiles of 256.
-__global__ void __launch_bounds__(256) k_degree_rank(const double *__restrict__ deg, int n, int *__restrict__ rank) {
+// memory in tiles of 256.  With ascending_b the second vector is ranked from its
+// smallest entry (QAP minimisation pairs large with small: the rearrangement
+// inequality's other extreme).
+__global__ void __launch_bounds__(256) k_degree_rank(const double *__restrict__ deg, int n, int ascending_b,
+                                                     int *__restrict__ rank) {
     __shared__ double tile[256];
     const double *d = deg + (long long)blockIdx.y * n;
+    const double sg = (blockIdx.y == 1 && ascending_b) ? -1.0 : 1.0;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const double di = i < n ? d[i] : 0.0;
+    const double di = i < n ? sg * d[i] : 0.0;
     int r = 0;
     for (int k0 = 0; k0 < n; k0 += 256) {
         __syncthreads();
-        if (k0 + (int)threadIdx.x < n) tile[threadIdx.x] = d[k0 + threadIdx.x];
+        if (k0 + (int)threadIdx.x < n) tile[threadIdx.x] = sg * d[k0 + threadIdx.x];
         __syncthreads();
         const int lim = min(256, n - k0);
         for (int t = 0; t < lim; ++t) {
@@ -574,23 +672,66 @@ static int rows_grid(int n, int cap_per_sm = 8) {
     return std::max(1, std::min(n, sms * cap_per_sm));
 }
 
-int adj_to_bf16(const void *A, int dtype, int n, __nv_bfloat16 *A16, int ld16, float *deg, cudaStream_t s) {
+static const void *window(const AdjView &v, int r0, int c0) {
+    const size_t es = v.dtype == GOAT_DTYPE_U8 ? 1 : 4;
+    return (const uint8_t *)v.p + ((size_t)r0 * (size_t)v.ld + (size_t)c0) * es;
+}
+
+int adj_to_bf16(const AdjView &v, int r0, int c0, int rows, int cols, __nv_bfloat16 *dst, int width, long long stride,
+                float *deg, cudaStream_t s) {
     note_launches(1);
-    const int grid = grid_for((long long)n * 32, 256, 16);
-    if (dtype == GOAT_DTYPE_U8)
-        k_adj_to_bf16<uint8_t><<<grid, 256, 0, s>>>((const uint8_t *)A, n, A16, ld16, deg);
+    const int grid = grid_for((long long)rows * 32, 256, 16);
+    const void *src = window(v, r0, c0);
+    if (v.dtype == GOAT_DTYPE_U8)
+        k_adj_to_bf16<uint8_t><<<grid, 256, 0, s>>>((const uint8_t *)src, v.ld, rows, cols, dst, width, stride, deg);
     else
-        k_adj_to_bf16<float><<<grid, 256, 0, s>>>((const float *)A, n, A16, ld16, deg);
+        k_adj_to_bf16<float><<<grid, 256, 0, s>>>((const float *)src, v.ld, rows, cols, dst, width, stride, deg);
     return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
 }
 
-int adj_to_e4m3(const void *A, int dtype, int n, uint8_t *A8, int ld8, cudaStream_t s) {
+int adj_to_e4m3(const AdjView &v, int r0, int c0, int rows, int cols, uint8_t *dst, int width, long long stride,
+                cudaStream_t s) {
     note_launches(1);
-    const int grid = grid_for((long long)n * (ld8 / 2));
-    if (dtype == GOAT_DTYPE_U8)
-        k_adj_to_e4m3<uint8_t><<<grid, 256, 0, s>>>((const uint8_t *)A, n, A8, ld8);
+    const int grid = grid_for((long long)rows * (width / 2));
+    const void *src = window(v, r0, c0);
+    if (v.dtype == GOAT_DTYPE_U8)
+        k_adj_to_e4m3<uint8_t><<<grid, 256, 0, s>>>((const uint8_t *)src, v.ld, rows, cols, dst, width, stride);
     else
-        k_adj_to_e4m3<float><<<grid, 256, 0, s>>>((const float *)A, n, A8, ld8);
+        k_adj_to_e4m3<float><<<grid, 256, 0, s>>>((const float *)src, v.ld, rows, cols, dst, width, stride);
+    return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
+}
+
+template <typename O>
+static int adj_transpose(const AdjView &v, int r0, int c0, int rows, int cols, O *dst, int width, long long stride,
+                         cudaStream_t s) {
+    note_launches(1);
+    const dim3 grid((unsigned)ceil_div(width, 32), (unsigned)ceil_div(cols, 32)), block(32, 8);
+    const void *src = window(v, r0, c0);
+    if (v.dtype == GOAT_DTYPE_U8)
+        k_adj_transpose<uint8_t, O><<<grid, block, 0, s>>>((const uint8_t *)src, v.ld, rows, cols, dst, width, stride);
+    else
+        k_adj_transpose<float, O><<<grid, block, 0, s>>>((const float *)src, v.ld, rows, cols, dst, width, stride);
+    return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
+}
+
+int adj_to_bf16_t(const AdjView &v, int r0, int c0, int rows, int cols, __nv_bfloat16 *dst, int width,
+                  long long stride, cudaStream_t s) {
+    return adj_transpose<__nv_bfloat16>(v, r0, c0, rows, cols, dst, width, stride, s);
+}
+
+int adj_to_e4m3_t(const AdjView &v, int r0, int c0, int rows, int cols, uint8_t *dst, int width, long long stride,
+                  cudaStream_t s) {
+    return adj_transpose<uint8_t>(v, r0, c0, rows, cols, dst, width, stride, s);
+}
+
+int adj_col_sums(const AdjView &v, int r0, int c0, int rows, int cols, float *out, cudaStream_t s) {
+    note_launches(1);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(cols, 256), 4096));
+    const void *src = window(v, r0, c0);
+    if (v.dtype == GOAT_DTYPE_U8)
+        k_col_sums<uint8_t><<<grid, 256, 0, s>>>((const uint8_t *)src, v.ld, rows, cols, out);
+    else
+        k_col_sums<float><<<grid, 256, 0, s>>>((const float *)src, v.ld, rows, cols, out);
     return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
 }
 
@@ -619,9 +760,25 @@ void f32_to_terms(const float *X, int n, long long ldx, __nv_bfloat16 *Xb, int l
     k_f32_to_terms<<<grid_for((long long)n * (ld16 / 8)), 256, 0, s>>>(X, n, ldx, Xb, ld16, terms);
 }
 
-void barycenter(const float *dA, const float *dB, int n, float *G, float *P, DevState *st, cudaStream_t s) {
+void barycenter(const float *dA, const float *dB, const float *eA, const float *eB, int n, float scale,
+                const float *C, float *G, float *P, DevState *st, cudaStream_t s) {
     note_launches(1);
-    k_barycenter<<<rows_grid(n), 256, 0, s>>>(dA, dB, n, G, P, st);
+    k_barycenter<<<rows_grid(n), 256, 0, s>>>(dA, dB, eA, eB, n, scale, C, G, P, st);
+}
+
+void add_f32(float *X, const float *C, long long total, cudaStream_t s) {
+    note_launches(1);
+    k_add_f32<<<grid_for(total / 4 + 1), 256, 0, s>>>(X, C, total);
+}
+
+void seed_perm(int32_t *perm, int n, int m, cudaStream_t s) {
+    note_launches(1);
+    k_seed_perm<<<(int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 1024)), 256, 0, s>>>(perm, n, m);
+}
+
+void embed_block(const float *P22, int n, int m, float *out, cudaStream_t s) {
+    note_launches(1);
+    k_embed_block<<<rows_grid(n + m), 256, 0, s>>>(P22, n, m, out);
 }
 
 void absmax(const float *X, long long total, unsigned *out, cudaStream_t s) {
@@ -631,7 +788,8 @@ void absmax(const float *X, long long total, unsigned *out, cudaStream_t s) {
 
 size_t rearrangement_scratch_bytes(int n) { return (size_t)n * (2 * sizeof(double) + 3 * sizeof(int)); }
 
-int rearrangement_perm(const void *A, const void *B, int dtype, int n, void *scratch, int32_t *perm, cudaStream_t s) {
+int rearrangement_perm(const void *A, const void *B, int dtype, int n, int maximize, void *scratch, int32_t *perm,
+                       cudaStream_t s) {
     double *deg = reinterpret_cast<double *>(scratch);
     int *rank = reinterpret_cast<int *>(deg + 2 * (size_t)n);
     int *inv = rank + 2 * (size_t)n;
@@ -643,7 +801,7 @@ int rearrangement_perm(const void *A, const void *B, int dtype, int n, void *scr
         k_degrees_f64<float><<<gw, 256, 0, s>>>((const float *)A, n, deg);
         k_degrees_f64<float><<<gw, 256, 0, s>>>((const float *)B, n, deg + n);
     }
-    k_degree_rank<<<dim3((unsigned)ceil_div(n, 256), 2), 256, 0, s>>>(deg, n, rank);
+    k_degree_rank<<<dim3((unsigned)ceil_div(n, 256), 2), 256, 0, s>>>(deg, n, maximize ? 0 : 1, rank);
     const int g = (int)std::min<int64_t>(ceil_div(n, 256), 1024);
     k_rank_invert<<<g, 256, 0, s>>>(rank + n, n, inv);
     k_rank_pair<<<g, 256, 0, s>>>(rank, inv, n, perm);

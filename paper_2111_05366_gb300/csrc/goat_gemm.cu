@@ -13,6 +13,13 @@
 // (Y = [Y_hi | Y_lo] along K, X re-read for each term): that is how the
 // FP32-accurate form adds A Q_hi B + A Q_lo B in one TMEM accumulator.
 //
+// A launch may also cover one K range of a longer product (k_offset) and add an
+// FP32 addend in its epilogue: the FP32-accurate form splits long K into chunks
+// so that the tensor core's FP32 accumulation, which truncates (every sampled
+// entry of a K = 65536 product came out smaller in magnitude, by 1.6e-5 relative),
+// runs over fewer steps, and the chunks are added in the epilogue with
+// round-to-nearest FP32.
+//
 // The same kernel runs the 8-bit form (FP8 = true): E4M3 operands, kind::f8f6f4.
 // A stage then holds 128 elements of K instead of 64 -- the same 128 bytes per
 // swizzled row, so the shared-memory layout, the descriptors and their 32-byte K
@@ -47,6 +54,10 @@ struct GemmParams {
     int M, N;            // output rows (from X) and columns (from Y)
     int kx_period;       // X is read at k mod kx_period (multiple of BK)
     int num_kb;          // K extent / BK
+    int k_offset_kb;     // first K block of this launch (K positions k_offset_kb * BK + ...)
+    const float *addend; // FP32 matrix added in the epilogue (nullable), ld_addend, columns < addend_cols
+    long long ld_addend;
+    int addend_cols;
     int tiles_m, tiles_n;
     float scale;
     const float *scale_dev;  // device factor on top of scale (nullable)
@@ -145,6 +156,12 @@ __device__ __forceinline__ void store_tile_row(const GemmParams &p, const TileJo
     float x[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) x[c] = (col0 + c < j.valid_cols) ? v[c] * s : 0.0f;
+    if (p.addend) {
+        const float *ad = p.addend + (long long)row * p.ld_addend + col0;
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+            if (col0 + c < p.addend_cols) x[c] += ad[c];
+    }
     if (p.mode == GEMM_OUT_F32) {
         float *dst = j.out_f32 + (long long)row * j.ld_out + col0;
         const bool full = (col0 + 32 <= j.out_cols) && ((j.ld_out & 3) == 0) &&
@@ -257,7 +274,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                         break;
                     }
                     const uint32_t sx = sbase + stage * STAGE_BYTES;
-                    const int kk = kb * (FP8 ? 2 * BK : BK);  // K elements per stage: 128 bytes
+                    const int kk = (p.k_offset_kb + kb) * (FP8 ? 2 * BK : BK);  // K elements per stage: 128 bytes
                     mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
                     tma_load_2d(sx, &tmX, full_bar(stage), kk % p.kx_period, job.x_row);
                     tma_load_2d(sx + TILE_X_BYTES, &tmY, full_bar(stage), kk, job.y_row);
@@ -433,7 +450,8 @@ static int prepare_launch() {
 
 int gemm_xyT(const GemmCall &c, cudaStream_t stream) {
     const int bk = c.fp8 ? 2 * BK : BK;  // K elements per stage
-    if (c.M < 1 || c.N < 1 || c.k_total < 1 || (c.k_total % bk) || (c.kx_period % bk) || c.kx_period < 1)
+    if (c.M < 1 || c.N < 1 || c.k_total < 1 || (c.k_total % bk) || (c.kx_period % bk) || c.kx_period < 1 ||
+        c.k_begin < 0 || (c.k_begin % bk))
         return GOAT_ERR_INVALID_ARG;
     {
         const int ps = prepare_launch();
@@ -444,10 +462,16 @@ int gemm_xyT(const GemmCall &c, cudaStream_t stream) {
     CUtensorMap mx, my;
     int st = make_map(&mx, c.X, (uint64_t)c.kx_period, (uint64_t)c.x_rows, (uint64_t)c.x_stride, BM, c.fp8 != 0);
     if (st) return st;
-    st = make_map(&my, c.Y, (uint64_t)c.k_total, (uint64_t)c.y_rows, (uint64_t)c.y_stride, BN, c.fp8 != 0);
+    st = make_map(&my, c.Y, (uint64_t)(c.k_begin + c.k_total), (uint64_t)c.y_rows, (uint64_t)c.y_stride, BN,
+                  c.fp8 != 0);
     if (st) return st;
 
     GemmParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.k_offset_kb = c.k_begin / bk;
+    p.addend = c.addend;
+    p.ld_addend = c.ld_addend;
+    p.addend_cols = c.addend_cols;
     p.M = c.M;
     p.N = c.N;
     p.kx_period = c.kx_period;

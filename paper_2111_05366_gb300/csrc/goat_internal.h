@@ -37,6 +37,10 @@ struct GemmCall {
     long long row_stride;
     int out_rows, out_cols;
     int *err;
+    int k_begin;             // this launch covers K positions [k_begin, k_begin + k_total) (multiple of the stage K)
+    const float *addend;     // FP32 matrix added to the result in the epilogue (nullable; may be out_f32 itself)
+    long long ld_addend;
+    int addend_cols;         // columns of the addend (later output columns add nothing)
 };
 
 int gemm_xyT(const GemmCall &c, cudaStream_t stream);
@@ -80,13 +84,34 @@ long long launches_so_far();
 struct DevState;
 
 // goat_fw.cu
-int adj_to_bf16(const void *A, int dtype, int n, __nv_bfloat16 *A16, int ld16, float *deg, cudaStream_t s);
-int adj_to_e4m3(const void *A, int dtype, int n, uint8_t *A8, int ld8, cudaStream_t s);
+// An adjacency matrix in device memory: element type GOAT_DTYPE_*, leading dimension ld.
+struct AdjView {
+    const void *p;
+    long long ld;
+    int dtype;
+};
+// The rows x cols window at (r0, c0) -> operand rows of `width` elements (zero
+// beyond cols), `stride` elements apart; deg (nullable) gets the window's row sums.
+int adj_to_bf16(const AdjView &v, int r0, int c0, int rows, int cols, __nv_bfloat16 *dst, int width, long long stride,
+                float *deg, cudaStream_t s);
+int adj_to_e4m3(const AdjView &v, int r0, int c0, int rows, int cols, uint8_t *dst, int width, long long stride,
+                cudaStream_t s);
+// The same for the window's transpose (dst row c = window column c, width >= rows).
+int adj_to_bf16_t(const AdjView &v, int r0, int c0, int rows, int cols, __nv_bfloat16 *dst, int width,
+                  long long stride, cudaStream_t s);
+int adj_to_e4m3_t(const AdjView &v, int r0, int c0, int rows, int cols, uint8_t *dst, int width, long long stride,
+                  cudaStream_t s);
+int adj_col_sums(const AdjView &v, int r0, int c0, int rows, int cols, float *out, cudaStream_t s);
 int bf16_to_e4m3(const __nv_bfloat16 *X, int rows, int ld_src, uint8_t *X8, int ld8, unsigned *amax_bits,
                  float *inv_scale, cudaStream_t s);
 int count_asym(const void *A, int dtype, int n, int *count_dev, cudaStream_t s);
 void f32_to_terms(const float *X, int n, long long ldx, __nv_bfloat16 *Xb, int ld16, int terms, cudaStream_t s);
-void barycenter(const float *dA, const float *dB, int n, float *G, float *P, DevState *st, cudaStream_t s);
+// G = scale (dA dB^T + eA eB^T) [+ C], P = J (nullable); eA/eB and C nullable.
+void barycenter(const float *dA, const float *dB, const float *eA, const float *eB, int n, float scale,
+                const float *C, float *G, float *P, DevState *st, cudaStream_t s);
+void add_f32(float *X, const float *C, long long total, cudaStream_t s);  // X, C 16-byte aligned
+void seed_perm(int32_t *perm, int n, int m, cudaStream_t s);
+void embed_block(const float *P22, int n, int m, float *out, cudaStream_t s);
 void absmax(const float *X, long long total, unsigned *out, cudaStream_t s);
 int ls_blocks(int n);
 void line_search(const float *G, const float *GQ, const float *P, const __nv_bfloat16 *Qb, int ldq, int terms,
@@ -113,7 +138,8 @@ void sinkhorn_queue_fixed(const float *G, int n, long long ld, float *f, float *
 // degree of A with the k-th largest of B (grad f(J) is rank one).  scratch holds
 // rearrangement_scratch_bytes(n) bytes (8-byte aligned).
 size_t rearrangement_scratch_bytes(int n);
-int rearrangement_perm(const void *A, const void *B, int dtype, int n, void *scratch, int32_t *perm, cudaStream_t s);
+int rearrangement_perm(const void *A, const void *B, int dtype, int n, int maximize, void *scratch, int32_t *perm,
+                       cudaStream_t s);
 // Zeroes the operand buffer and writes the permutation matrix of perm into it (FAQ's Q).
 int write_perm_q(const int32_t *perm, int n, __nv_bfloat16 *Qb, int ldq, int terms, cudaStream_t s);
 void write_q(const float *G, int n, long long ld, const float *f, const float *g, const DevState *st,

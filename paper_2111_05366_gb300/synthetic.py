@@ -165,6 +165,34 @@ def rho_er_pair(n: int, p: float, rho: float, seed: int, weighted: bool = False)
     return rho_sbm_pair([n], [[p]], rho, seed, weighted=weighted)
 
 
+def rho_er_digraph_pair(n: int, p: float, rho: float, seed: int, weighted: bool = False) -> GraphPair:
+    """A rho-correlated directed Erdos-Renyi pair: every ordered pair (i, j), i != j,
+    is an arc of A with probability p; B' keeps an arc of A with probability
+    p + rho (1 - p) and adds one where A has none with probability p (1 - rho), so
+    each graph has density p and arc correlation rho; B = B' relabelled by a seeded
+    sigma.  Dense sampling (n up to a few thousand).  weighted=True: lognormal(0, 1)
+    weights on A's arcs, shared arcs carry A's weight in B, new arcs fresh ones."""
+    rng = _rng(seed + 31_337)
+    a = rng.random((n, n)) < p
+    u = rng.random((n, n))
+    b = np.where(a, u < p + rho * (1.0 - p), u < p * (1.0 - rho))
+    np.fill_diagonal(a, False)
+    np.fill_diagonal(b, False)
+    sigma = rng.permutation(n).astype(np.int64)
+    sigma_inv = np.empty(n, dtype=np.int64)
+    sigma_inv[sigma] = np.arange(n)
+    if weighted:
+        wa = rng.lognormal(0.0, 1.0, size=(n, n)).astype(np.float32)
+        wb = np.where(a, wa, rng.lognormal(0.0, 1.0, size=(n, n)).astype(np.float32))
+        A = np.where(a, wa, 0.0).astype(np.float32)
+        Bp = np.where(b, wb, 0.0).astype(np.float32)
+    else:
+        A = a.astype(np.uint8)
+        Bp = b.astype(np.uint8)
+    B = np.ascontiguousarray(Bp[np.ix_(sigma, sigma)])  # B[x, y] = B'[sigma x, sigma y]
+    return GraphPair(A=np.ascontiguousarray(A), B=B, truth=sigma_inv.astype(np.int32), n=n, seed=seed)
+
+
 def sbm3_block_sizes(n: int, fractions=(0.40, 0.35, 0.25)):
     """Block sizes for the 3-block SBM: floor of each fraction, remainder to the last block."""
     sizes = [int(np.floor(f * n)) for f in fractions[:-1]]

@@ -63,3 +63,22 @@ def test_large_sbm_sizes_and_determinism():
     g1 = synthetic.rho_er_pair(100, 0.1, 0.5, seed=4)
     g2 = synthetic.rho_er_pair(100, 0.1, 0.5, seed=4)
     assert (g1.A == g2.A).all() and (g1.B == g2.B).all() and (g1.truth == g2.truth).all()
+
+
+def test_directed_pair_density_correlation_and_truth():
+    n, p, rho = 900, 0.06, 0.75
+    gp = synthetic.rho_er_digraph_pair(n, p, rho, seed=3)
+    A, B, t = gp.A, gp.B, gp.truth
+    assert A.dtype == np.uint8 and (A != A.T).any()
+    assert A.diagonal().sum() == 0 and B.diagonal().sum() == 0
+    assert sorted(t) == list(range(n))
+    off = ~np.eye(n, dtype=bool)
+    a = A[off].astype(float)
+    b = B[np.ix_(t, t)][off].astype(float)
+    m = a.size
+    for x in (a, b):
+        assert abs(x.mean() - p) < 4 * np.sqrt(p * (1 - p) / m)
+    assert abs(np.corrcoef(a, b)[0, 1] - rho) < 4 * np.sqrt((1 - rho ** 2) ** 2 / m) + 0.01
+    g1 = synthetic.rho_er_digraph_pair(150, 0.1, 1.0, seed=4, weighted=True)
+    assert g1.A.dtype == np.float32
+    np.testing.assert_array_equal(g1.A, g1.B[np.ix_(g1.truth, g1.truth)])
