@@ -55,13 +55,16 @@ def parse():
     ap.add_argument("--sk-max-iter", type=int, default=500)
     ap.add_argument("--seed", type=int, default=3000)
     ap.add_argument("--plain-steps", type=int, default=1)
-    ap.add_argument("--chosen", choices=["fp8", "bf16"], default="fp8",
-                    help="product form of the timed (chosen) solve; the other 16/8-bit form is reported beside it")
+    ap.add_argument("--chosen", choices=["bf16split", "fp8", "bf16"], default="bf16split",
+                    help="product form of the timed (chosen) solve; the other forms are reported beside it")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-rows", type=int, default=4)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--accuracy-seeds", type=int, default=20,
+                    help="n = 1500 SBM pairs per rho in the accuracy comparison (the oracle's values are stored)")
     ap.add_argument("--pairs", type=int, default=512)
     ap.add_argument("--restarts", type=int, default=20)
     ap.add_argument("--train-pairs", type=int, default=48)
@@ -69,7 +72,7 @@ def parse():
                     default=None,
                     help="run only one step kind a few times on the workload (the small cases profiled with ncu)")
     ap.add_argument("--repeat", type=int, default=3)
-    ap.add_argument("--precision", choices=["bf16", "fp8", "fp32"], default="bf16",
+    ap.add_argument("--precision", choices=["bf16", "fp8", "fp32", "bf16split"], default="bf16",
                     help="form of the products in --kernel-case gemm")
     return ap.parse_args()
 
@@ -173,6 +176,115 @@ def gemm_traffic_per_launch(n: int, name: str = "k_gemm_xyT_traffic.txt"):
     return bytes_ * (n / n_cap) ** 3 if n != n_cap else bytes_
 
 
+# ------------------------------------------------------------------ per-form report
+
+FORM_PRECISION = {"fp8": 2, "bf16": 0, "fp32": 1, "bf16split": 3}
+# BF16 MMA passes of (product 1, product 2) relative to one n x n x n BF16 product:
+# the FP32 form splits Q and Q B in two terms (K = 2n in both products), the split
+# form only Q B (product 2); the 8-bit form runs its passes at twice the BF16 rate
+FORM_PASSES = {"fp8": (1.0, 1.0), "bf16": (1.0, 1.0), "fp32": (2.0, 2.0), "bf16split": (1.0, 2.0)}
+
+
+def gemm_roofline(precision: str, n: int, ms_per_launch: float, peaks: dict, nnz: float):
+    """Roofline block of the tensor-core products of one precision form.  The FP32
+    form runs each product as BF16 MMAs over K = 2n (two split terms): its executed
+    work is 2 x 2 n^3 BF16 FLOP per launch, which is what the tensor pipe sees."""
+    flop = 2.0 * n ** 3
+    executed = flop * sum(FORM_PASSES[precision]) / 2.0  # mean over the two products
+    if precision == "fp8":
+        # no FP8 peak was measured on this pool: the measured BF16 sustained rate times
+        # the nominal dense FP8 / BF16 ratio (4.5 / 2.25 PFLOP/s)
+        peak = 2.0 * peaks["bf16_tflops_sustained"]
+        kernel = "k_gemm_xyT (E4M3 kind::f8f6f4, one n x n x n product per launch)"
+        peak_source = f"{peaks['source']} bf16_tflops_sustained x nominal fp8/bf16 ratio 2"
+        traffic = gemm_traffic_per_launch(n, "k_gemm_xyT_fp8_traffic.txt")
+    else:
+        peak = peaks["bf16_tflops_sustained"]
+        kernel = {"bf16": "k_gemm_xyT (BF16 kind::f16, one n x n x n product per launch)",
+                  "bf16split": "k_gemm_xyT (BF16 kind::f16; product 2 over the two terms of Q B, K = 2n)",
+                  "fp32": "k_gemm_xyT (BF16 kind::f16 over two split terms, K = 2n, in K chunks)"}[precision]
+        peak_source = f"{peaks['source']} bf16_tflops_sustained"
+        traffic = gemm_traffic_per_launch(n) if precision == "bf16" else None
+    sec = ms_per_launch / 1000.0
+    achieved = executed / sec / 1e12
+    # A and B are ~1 % dense: of the dense FLOP only 2 nnz(B) n (C1 = B Q^T) and
+    # 2 nnz(A) n (A C1^T) multiply a nonzero
+    return {"bound": "tensor", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_source,
+            "algorithmic_flop_per_launch": flop, "executed_flop_per_launch": executed,
+            "useful_flop_per_launch": nnz * n, "useful_tflops": nnz * n / sec / 1e12}
+
+
+def form_report(outs, ms: float, precision: str, n: int, peaks: dict, nnz: float, truth) -> dict:
+    """FW iterations per second, time to solution and per-phase figures of the solves
+    `outs` (goat_match results) that took `ms` of device time."""
+    solves = len(outs)
+    it = sum(o[2]["fw_iters"] for o in outs)
+    ms_gemm = sum(o[2]["ms_gemm"] for o in outs)
+    n_gemm = max(sum(o[2]["gemm_launches"] for o in outs), 1)
+    ms_fw = sum(o[2]["ms_fw"] for o in outs)
+    ms_sk = sum(o[2]["ms_sinkhorn"] for o in outs)
+    sk = sum(o[2]["sk_iters_total"] for o in outs)
+    rep = {"precision": precision, "value": it / (ms / 1000.0), "unit": UNIT,
+           "fw_loop_value": it / (ms_fw / 1000.0), "ms_per_solve": ms / solves,
+           "fw_iters_per_solve": it / solves, "sinkhorn_iters_per_fw_iter": sk / max(it, 1),
+           "gemm_ms_per_launch": ms_gemm / n_gemm, "ms_projection_per_solve": sum(o[2]["ms_project"] for o in outs) / solves,
+           "accuracy": float((outs[-1][0] == truth).mean()), "objective": outs[-1][2]["objective"],
+           "lap_gap": outs[-1][2]["lap_gap"],
+           "roofline": gemm_roofline(precision, n, ms_gemm / n_gemm, peaks, nnz)}
+    if sk:
+        t_it = ms_sk / sk / 1000.0
+        # algorithmic bytes of one Sinkhorn iteration: one read of FP32 G (4 n^2); the
+        # two-pass form reads it twice (8 n^2)
+        rep["sinkhorn_algorithmic_gbs"] = 4.0 * n * n / t_it / 1e9
+        rep["sinkhorn_dram_gbs_two_pass"] = 8.0 * n * n / t_it / 1e9
+    return rep
+
+
+# The paper's Sec. 4.3 rho-SBM at n = 1500 (3 equal blocks), where GOAT recovers a
+# real fraction of the vertices: the forms' matching accuracy is compared there with
+# the FP64 oracle's, stored in tests/golden/sbm1500_oracle.txt by the committed
+# script beside it (bench.py itself never runs the oracle outside its CPU legs).
+SBM1500_PB = [[0.2, 0.01, 0.01], [0.01, 0.1, 0.01], [0.01, 0.01, 0.2]]
+
+
+def sbm1500_oracle_accuracy():
+    path = os.path.join(ROOT, "tests", "golden", "sbm1500_oracle.txt")
+    out = {}
+    if not os.path.exists(path):
+        return out
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        rho, seed, acc, obj, it = line.split()
+        out[(float(rho), int(seed))] = float(acc)
+    return out
+
+
+def accuracy_comparison(goat, synthetic, torch, forms: dict, seeds: int) -> dict:
+    """Each form's mean matching accuracy on the n = 1500 pairs (seeds 1..seeds) next
+    to the oracle's stored accuracy on the same pairs, in percentage points."""
+    ref = sbm1500_oracle_accuracy()
+    res = {"workload": "rho-SBM n=1500, 3 equal blocks, B=[[.2,.01,.01],[.01,.1,.01],[.01,.01,.2]] (Sec. 4.3)",
+           "seeds": seeds, "rho": {}}
+    for rho in (0.9, 0.95):
+        row = {}
+        pairs = [synthetic.rho_sbm_pair([500, 500, 500], SBM1500_PB, rho, seed=s) for s in range(1, seeds + 1)]
+        for name, prm in forms.items():
+            accs = []
+            for gp in pairs:
+                perm, _, _ = goat.goat_match(torch.from_numpy(gp.A).cuda(), torch.from_numpy(gp.B).cuda(),
+                                             eps_rel=0.03, max_iter=30, tol=1e-4, params=prm)
+                accs.append(float((perm == gp.truth).mean()))
+            row[name] = float(np.mean(accs))
+        refs = [ref.get((rho, s)) for s in range(1, seeds + 1)]
+        if all(r is not None for r in refs):
+            row["oracle"] = float(np.mean(refs))
+            row["max_abs_delta_points"] = max(abs(v - row["oracle"]) * 100 for k, v in row.items() if k != "oracle")
+        res["rho"][str(rho)] = row
+    return res
+
+
 # ------------------------------------------------------------------ CPU oracle sample
 
 def cpu_oracle_sample(gp, rows: int, sk_iters_per_fw: float):
@@ -267,7 +379,7 @@ def run_kernel_case(args):
     out = {"case": args.kernel_case, "n": n}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if args.kernel_case == "gemm":
-        prec = {"bf16": goat.GOAT_PREC_BF16, "fp8": goat.GOAT_PREC_FP8, "fp32": goat.GOAT_PREC_FP32}[args.precision]
+        prec = FORM_PRECISION[args.precision]
         G = goat.goat_gradient(A, B, P, precision=prec)
         e0.record()
         for _ in range(args.repeat):
@@ -275,7 +387,7 @@ def run_kernel_case(args):
         e1.record()
         out["precision"] = args.precision
     elif args.kernel_case == "faq":
-        prec = {"bf16": goat.GOAT_PREC_BF16, "fp8": goat.GOAT_PREC_FP8, "fp32": goat.GOAT_PREC_FP32}[args.precision]
+        prec = FORM_PRECISION[args.precision]
         del P
         out["precision"] = args.precision
         for name, direction in (("goat", goat.GOAT_DIR_LOT), ("faq", goat.GOAT_DIR_LAP)):
@@ -530,17 +642,18 @@ def main():
     log(f"pair ready: {nnz_A} + {nnz_B} nonzeros")
     A = torch.from_numpy(gp.A).cuda()
     B = torch.from_numpy(gp.B).cuda()
-    ws = torch.empty(max(goat.workspace_bytes(n, goat.GOAT_DTYPE_U8, pr) for pr in
-                         (goat.GOAT_PREC_FP32, goat.GOAT_PREC_FP8, goat.GOAT_PREC_BF16)), dtype=torch.uint8,
-                     device="cuda")
-    chosen_prec = goat.GOAT_PREC_FP8 if args.chosen == "fp8" else goat.GOAT_PREC_BF16
-    other_prec = goat.GOAT_PREC_BF16 if args.chosen == "fp8" else goat.GOAT_PREC_FP8
-    other = goat.default_params(precision=other_prec, sk_warm_start=1, sk_tol=args.sk_tol,
-                                sk_max_iter=args.sk_max_iter, profile=1)
+    ws = torch.empty(max(goat.workspace_bytes(n, goat.GOAT_DTYPE_U8, pr) for pr in FORM_PRECISION.values()),
+                     dtype=torch.uint8, device="cuda")
+    chosen_prec = FORM_PRECISION[args.chosen]
     chosen = goat.default_params(precision=chosen_prec, sk_warm_start=1, sk_tol=args.sk_tol,
                                  sk_max_iter=args.sk_max_iter, profile=1)
+    others = {f"{k}_warm": goat.default_params(precision=FORM_PRECISION[k], sk_warm_start=1, sk_tol=args.sk_tol,
+                                               sk_max_iter=args.sk_max_iter, profile=1)
+              for k in ("bf16split", "bf16", "fp8") if k != args.chosen}
     plain = goat.default_params(precision=goat.GOAT_PREC_FP32, sk_warm_start=0, sk_tol=args.sk_tol,
                                 sk_max_iter=args.sk_max_iter, profile=1)
+    plain_warm = goat.default_params(precision=goat.GOAT_PREC_FP32, sk_warm_start=1, sk_tol=args.sk_tol,
+                                     sk_max_iter=args.sk_max_iter, profile=1)
 
     def solve(params):
         return goat.goat_match(A, B, eps_rel=0.03, max_iter=args.max_iter, tol=args.fw_tol, params=params,
@@ -577,6 +690,10 @@ def main():
     acc = float((outs[-1][0] == gp.truth).mean())
 
     # per-phase breakdown and the roofline of the dominant kernel (the tensor-core products)
+    peaks = measured_peaks()
+    nnz = float(nnz_A + nnz_B)
+    chosen_rep = form_report(outs, ms, args.chosen, n, peaks, nnz, gp.truth)
+    roofline = chosen_rep["roofline"]
     ms_gemm = sum(o[2]["ms_gemm"] for o in outs)
     n_gemm = sum(o[2]["gemm_launches"] for o in outs)
     ms_sk = sum(o[2]["ms_sinkhorn"] for o in outs)
@@ -584,31 +701,6 @@ def main():
     ms_proj = sum(o[2]["ms_project"] for o in outs)
     sk_total = sum(o[2]["sk_iters_total"] for o in outs)
     launches = sum(o[2]["launches"] for o in outs)
-    peaks = measured_peaks()
-    flop_per_launch = 2.0 * n ** 3
-    achieved = flop_per_launch / (ms_gemm / max(n_gemm, 1) / 1000.0) / 1e12
-    if args.chosen == "fp8":
-        # no FP8 peak was measured on this machine: the measured BF16 sustained rate times
-        # the nominal dense FP8 / BF16 ratio (4.5 / 2.25 PFLOP/s)
-        peak = 2.0 * peaks["bf16_tflops_sustained"]
-        kernel = "k_gemm_xyT (E4M3 kind::f8f6f4, one n x n x n product per launch)"
-        peak_source = f"{peaks['source']} bf16_tflops_sustained x nominal fp8/bf16 ratio 2"
-        traffic = gemm_traffic_per_launch(n, "k_gemm_xyT_fp8_traffic.txt")
-    else:
-        peak = peaks["bf16_tflops_sustained"]
-        kernel = "k_gemm_xyT (BF16 kind::f16, one n x n x n product per launch)"
-        peak_source = f"{peaks['source']} bf16_tflops_sustained"
-        traffic = gemm_traffic_per_launch(n)
-    # A and B are ~1 % dense: the products do 2 n^3 dense FLOP, of which only
-    # 2 nnz(B) n (C1 = B Q^T) and 2 nnz(A) n (A C1^T) multiply a nonzero
-    useful_per_launch = float(nnz_A + nnz_B) * n
-    roofline = {"bound": "tensor", "kernel": kernel,
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_source": peak_source,
-                "algorithmic_flop_per_launch": flop_per_launch,
-                "useful_flop_per_launch": useful_per_launch,
-                "useful_tflops": useful_per_launch / (ms_gemm / max(n_gemm, 1) / 1000.0) / 1e12}
-
     ms_fw_loop = sum(o[2]["ms_fw"] for o in outs)
     breakdown = {"ms_per_fw_iter": ms / max(fw_iters, 1), "gemm_ms_per_launch": ms_gemm / max(n_gemm, 1),
                  "ms_fw_loop_per_solve": ms_fw_loop / args.steps, "ms_projection_per_solve": ms_proj / args.steps,
@@ -619,50 +711,60 @@ def main():
                  "lap_rounds": st["lap_rounds"], "lap_tail_bids": st["lap_tail_bids"],
                  "lap_sap_rows": st["lap_sap_rows"], "lap_sap_pops": st["lap_sap_pops"],
                  "lap_ms_head": st["lap_ms_head"], "lap_ms_tail": st["lap_ms_tail"], "lap_ms_sap": st["lap_ms_sap"]}
-    if sk_total:
-        # one Sinkhorn iteration reads G twice (row pass + column pass): 8 n^2 bytes
-        breakdown["sinkhorn_gbs_two_pass"] = 8.0 * n * n / (ms_sk / sk_total / 1000.0) / 1e9
+    for k in ("sinkhorn_algorithmic_gbs", "sinkhorn_dram_gbs_two_pass"):
+        if k in chosen_rep:
+            breakdown[k] = chosen_rep[k]
 
     fw_loop_value = sum_over_ranks(float(fw_iters)) / (max_over_ranks(ms_fw_loop) / 1000.0)
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
               "scaling": "weak", "vs_baseline": None, "dtype": "e4m3" if args.chosen == "fp8" else "bf16",
+              "precision_form": {"bf16split": "BF16 products, Q B kept as two BF16 terms (GOAT_PREC_BF16_SPLIT)",
+                                 "bf16": "BF16 products (GOAT_PREC_BF16)",
+                                 "fp8": "E4M3 products (GOAT_PREC_FP8)"}[args.chosen],
               "data": "synthetic",
               "config": workload_config(args), "clocks": clocks, "gpu_launches": int(sum_over_ranks(launches)),
               "roofline": roofline, "breakdown": breakdown,
               # the Frank-Wolfe iterations alone (rows a1-a5): the projection runs once per
               # solve and is reported separately in breakdown.ms_projection_per_solve
-              "fw_loop": {"value": fw_loop_value, "unit": UNIT}}
+              "fw_loop": {"value": fw_loop_value, "unit": UNIT},
+              "warm_start": "each Sinkhorn solve starts from the previous Frank-Wolfe step's duals; the learned "
+                            "(MLP) start is measured separately (bench.py --kernel-case warmstart)"}
 
-    # the other 16/8-bit form on the same pair (one solve)
+    # every form on the same pair, one timed solve each after one untimed one: the other
+    # 16/8-bit form, and the plain FP32-accurate form cold- and warm-started, so that the
+    # gain of the precision and the gain of warm-starting the duals show separately
+    forms = {f"{args.chosen}_warm": chosen_rep}
     if not args.no_plain:
-        ms_o, outs_o, _ = timed(other, 1, 1)
-        log(f"{'bf16' if args.chosen == 'fp8' else 'fp8'} form timed: {ms_o:.0f} ms")
-        it_o = sum(o[2]["fw_iters"] for o in outs_o)
-        result["other_form"] = {
-            "precision": "bf16" if args.chosen == "fp8" else "fp8",
-            "value": it_o / (ms_o / 1000.0), "unit": UNIT,
-            "fw_loop_value": it_o / (sum(o[2]["ms_fw"] for o in outs_o) / 1000.0),
-            "accuracy": float((outs_o[-1][0] == gp.truth).mean()),
-            "gemm_ms_per_launch": sum(o[2]["ms_gemm"] for o in outs_o) / max(sum(o[2]["gemm_launches"] for o in outs_o), 1),
-            "ms_projection": outs_o[-1][2]["ms_project"]}
-
-    # plain FP32-accurate GPU form on the same pair
-    if not args.no_plain:
-        ms_p, outs_p, _ = timed(plain, 1, args.plain_steps)
-        log(f"plain form timed: {ms_p:.0f} ms")
-        it_p = sum(o[2]["fw_iters"] for o in outs_p)
-        v_p = sum_over_ranks(float(it_p)) / (max_over_ranks(ms_p) / 1000.0)
-        ms_fw_p = sum(o[2]["ms_fw"] for o in outs_p)
-        v_fw_p = sum_over_ranks(float(it_p)) / (max_over_ranks(ms_fw_p) / 1000.0)
-        result["fw_loop"]["plain_value"] = v_fw_p
-        result["fw_loop"]["chosen_over_plain"] = fw_loop_value / v_fw_p
-        result["plain_fp32"] = {"value": v_p, "unit": UNIT, "accuracy": float((outs_p[-1][0] == gp.truth).mean()),
-                                "fw_iters_per_solve": it_p / args.plain_steps,
-                                "sinkhorn_iters_per_fw_iter": sum(o[2]["sk_iters_total"] for o in outs_p) / max(it_p, 1),
-                                "gemm_ms_per_launch": sum(o[2]["ms_gemm"] for o in outs_p) /
-                                max(sum(o[2]["gemm_launches"] for o in outs_p), 1)}
-        result["chosen_over_plain"] = value / v_p
+        legs = [(name, prm, name[:-5]) for name, prm in others.items()]
+        legs += [("fp32_cold", plain, "fp32"), ("fp32_warm", plain_warm, "fp32")]
+        for name, prm, prec in legs:
+            ms_f, outs_f, _ = timed(prm, 1, args.plain_steps)
+            forms[name] = form_report(outs_f, ms_f, prec, n, peaks, nnz, gp.truth)
+            log(f"{name} form timed: {ms_f:.0f} ms ({forms[name]['fw_iters_per_solve']:.0f} FW iterations)")
+        cold = forms["fp32_cold"]
+        result["plain_fp32"] = {"value": cold["value"], "unit": UNIT, "accuracy": cold["accuracy"],
+                                "fw_iters_per_solve": cold["fw_iters_per_solve"],
+                                "sinkhorn_iters_per_fw_iter": cold["sinkhorn_iters_per_fw_iter"],
+                                "gemm_ms_per_launch": cold["gemm_ms_per_launch"]}
+        result["chosen_over_plain"] = value / cold["value"]
+        result["fw_loop"]["plain_value"] = cold["fw_loop_value"]
+        result["fw_loop"]["chosen_over_plain"] = fw_loop_value / cold["fw_loop_value"]
+        # the same ratios by time to solution (the forms run different numbers of FW
+        # iterations before the stop test ends them), against the cold and the warm plain form
+        result["time_to_solution"] = {
+            "ms": {k: v["ms_per_solve"] for k, v in forms.items()},
+            "chosen_speedup_vs_plain_cold": cold["ms_per_solve"] / chosen_rep["ms_per_solve"],
+            "chosen_speedup_vs_plain_warm": forms["fp32_warm"]["ms_per_solve"] / chosen_rep["ms_per_solve"],
+            "iters_per_s_ratio_vs_plain_cold": value / cold["value"],
+            "iters_per_s_ratio_vs_plain_warm": value / forms["fp32_warm"]["value"]}
+    result["forms"] = forms
+    if not args.no_accuracy and rank == 0:
+        acc_forms = {f"{k}_{'warm' if w else 'cold'}": goat.default_params(
+                         precision=FORM_PRECISION[k], sk_warm_start=w, sk_tol=args.sk_tol, sk_max_iter=args.sk_max_iter)
+                     for k in ("bf16split", "fp32", "bf16", "fp8") for w in (1, 0)}
+        result["accuracy"] = accuracy_comparison(goat, synthetic, torch, acc_forms, args.accuracy_seeds)
+        log(f"accuracy on the n=1500 SBM: {result['accuracy']['rho']}")
 
     # end to end through the host-buffer entry point: pinned host A, B in, permutation out
     if not args.no_e2e:

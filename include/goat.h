@@ -83,7 +83,15 @@ enum {
      * E4M3 under one power-of-two scale per matrix (largest entry near 448), FP32
      * accumulation; twice the BF16 MMA rate.  (E4M3 x BF16 is not one tensor-core
      * operation, so Q is 8-bit too.)  Gradient error ~1e-2 relative. */
-    GOAT_PREC_FP8 = 2
+    GOAT_PREC_FP8 = 2,
+    /* Q as one BF16 term, the intermediate Q B as two (hi + lo): three BF16 MMA
+     * passes per gradient instead of two (BF16) or four (FP32-accurate); the rounding
+     * of Q B, which the second product sums over only the degree, is removed. */
+    GOAT_PREC_BF16_SPLIT = 3,
+    /* the first product (C1 = B Q^T) in E4M3 (B exact, Q rounded under one
+     * power-of-two scale, twice the BF16 rate), C1 written as two BF16 terms for a
+     * BF16 second product: 2.5 BF16 MMA passes per gradient. */
+    GOAT_PREC_FP8_SPLIT = 4
 };
 
 /* direction step of each Frank-Wolfe iteration (goat_params.direction) */

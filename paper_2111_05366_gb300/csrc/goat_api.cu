@@ -40,7 +40,9 @@ struct Plan {
     size_t total;
     int n, m, n_full, dir;
     int ld;     // K extent of one operand part (multiple of 64; of 128 for directed graphs)
-    int terms;  // BF16 terms of Q and C1 (2 in the FP32-accurate form)
+    int terms;  // BF16 terms of Q (2 in the FP32-accurate form)
+    int tc;     // BF16 terms of C1 (2 in the FP32-accurate and the split-intermediate forms)
+    bool q8;    // first product in E4M3 (B and Q), second in BF16 over C1's two terms
     int ld8;    // E4M3 row width of Q (multiple of 128; equal to ld for directed graphs)
     int parts;  // 1, or 2 for directed graphs: A16 = [A | A^T], B16 = [B | B^T], C1 = [C1 | C1']
     int ldm;    // K extent of the seed term (multiple of 64)
@@ -66,6 +68,10 @@ static Plan make_plan(const Shape &sh, int dtype, int precision, int need) {
     w.ld = sh.dir ? (int)round_up(n, 128) : operand_ld(n);
     w.ld8 = (int)round_up(n, 128);  // an E4M3 stage holds 128 elements of K
     w.terms = precision == GOAT_PREC_FP32 ? 2 : 1;
+    w.tc = (precision == GOAT_PREC_FP32 || precision == GOAT_PREC_BF16_SPLIT || precision == GOAT_PREC_FP8_SPLIT)
+               ? 2
+               : 1;
+    w.q8 = precision == GOAT_PREC_FP8_SPLIT;  // 8-bit first product only
     w.fp8 = precision == GOAT_PREC_FP8;
     w.ldm = sh.m > 0 ? (int)round_up((int64_t)sh.m * w.parts, 64) : 0;
     w.state = take(sizeof(DevState));
@@ -75,8 +81,8 @@ static Plan make_plan(const Shape &sh, int dtype, int precision, int need) {
         w.A16 = take((size_t)n * w.parts * w.ld * 2);
         w.B16 = take((size_t)n * w.parts * w.ld * 2);
         w.Xq = take((size_t)n * w.terms * w.ld * 2);
-        w.C1 = take((size_t)n * w.parts * w.terms * w.ld * 2);
-        if (w.fp8) {
+        w.C1 = take((size_t)n * w.parts * w.tc * w.ld * 2);
+        if (w.fp8 || w.q8) {
             const size_t row8 = sh.dir ? 2 * (size_t)w.ld : (size_t)w.ld8;
             w.A8 = take((size_t)n * row8);
             w.B8 = take((size_t)n * row8);
@@ -317,9 +323,11 @@ static int gradient_bf16(const Plan &w, const Scratch &ws, float scale2, float *
     const int n = w.n;
     // the FP32-accurate form accumulates long K in chunks; G_out holds the partial
     // sums of product 1 (it is written only by product 2)
+    // (only the FP32-accurate form, terms = 2, needs the chunks: in the other forms the
+    // operands' rounding is far larger than the accumulation's)
     auto run = [&](const GemmCall &c) { return w.terms > 1 ? gemm_chunked(c, G_out, n, s) : gemm_xyT(c, s); };
-    const long long xs = (long long)w.parts * w.ld;            // row stride of A16, B16
-    const long long cs = (long long)w.parts * w.terms * w.ld;  // row stride of C1
+    const long long xs = (long long)w.parts * w.ld;         // row stride of A16, B16
+    const long long cs = (long long)w.parts * w.tc * w.ld;  // row stride of C1
     GemmCall c1;
     std::memset(&c1, 0, sizeof(c1));
     c1.X = ws.at<__nv_bfloat16>(w.B16);
@@ -335,16 +343,31 @@ static int gradient_bf16(const Plan &w, const Scratch &ws, float scale2, float *
     c1.scale = 1.0f;
     c1.mode = GEMM_OUT_BF16_TERMS;
     c1.out_b16 = ws.at<__nv_bfloat16>(w.C1);
-    c1.out_terms = w.terms;
+    c1.out_terms = w.tc;
     c1.term_stride = (long long)w.parts * w.ld;  // [C1_hi | C1'_hi | C1_lo | C1'_lo]
     c1.row_stride = cs;
     c1.out_rows = n;
     c1.out_cols = w.ld;  // the padding columns receive zeros
     c1.err = err;
+    if (w.q8) {
+        // first product in E4M3: B exact, Q rounded under one power-of-two scale; its
+        // output C1 still goes out as two BF16 terms for the BF16 second product
+        float *sc = ws.at<float>(w.f8s);
+        GOAT_TRY(bf16_to_e4m3(ws.at<__nv_bfloat16>(w.Xq), n, w.ld, ws.at<uint8_t>(w.Q8), w.ld8,
+                              reinterpret_cast<unsigned *>(sc), sc + 1, s));
+        c1.fp8 = 1;
+        c1.X = ws.at<uint8_t>(w.B8);
+        c1.x_stride = w.dir ? 2LL * w.ld : w.ld8;
+        c1.kx_period = w.ld8;
+        c1.Y = ws.at<uint8_t>(w.Q8);
+        c1.y_stride = w.ld8;
+        c1.k_total = w.ld8;
+        c1.scale_dev = sc + 1;
+    }
     GOAT_TRY(run(c1));
     if (w.dir) {
         GemmCall c1t = c1;
-        c1t.X = ws.at<__nv_bfloat16>(w.B16) + w.ld;
+        c1t.X = w.q8 ? (const void *)(ws.at<uint8_t>(w.B8) + w.ld8) : (const void *)(ws.at<__nv_bfloat16>(w.B16) + w.ld);
         c1t.out_b16 = ws.at<__nv_bfloat16>(w.C1) + w.ld;
         GOAT_TRY(run(c1t));
     }
@@ -353,7 +376,10 @@ static int gradient_bf16(const Plan &w, const Scratch &ws, float scale2, float *
     // K runs over [A | A^T] (period parts*ld) against C1's row: term t, part p at
     // offset (t * parts + p) ld, so position k meets A for p = 0 and A^T for p = 1
     GemmCall c2 = c1;
+    c2.fp8 = 0;
+    c2.scale_dev = nullptr;
     c2.X = ws.at<__nv_bfloat16>(w.A16);
+    c2.x_stride = xs;
     c2.kx_period = w.parts * w.ld;
     c2.Y = ws.at<__nv_bfloat16>(w.C1);
     c2.y_stride = cs;
@@ -398,7 +424,7 @@ static int prepare_operands(const AdjView &A, const AdjView &B, const Plan &w, c
                 GOAT_TRY(adj_col_sums(B, m, m, n, n, deg + 3 * (size_t)n, s));
             }
         }
-        if (w.fp8) {
+        if (w.fp8 || w.q8) {
             const int width = w.dir ? w.ld : w.ld8;
             const long long row8 = w.dir ? 2LL * w.ld : w.ld8;
             GOAT_TRY(adj_to_e4m3(A, m, m, n, n, ws.at<uint8_t>(w.A8), width, row8, s));
@@ -591,8 +617,11 @@ static int match_impl(const AdjView &A, const AdjView &B, const float *init, flo
         if (prof) cudaEventRecord(pe[2], s);
         GOAT_TRY(gradient_from_terms(w, ws, sigma, GQ, &st->error, s, prof ? pe[3] : nullptr));
         if (prof) cudaEventRecord(pe[4], s);
-        line_search(G, GQ, P, Xq, w.ld, w.terms, nullptr, n, partial, st, s);
-        fw_update(P, G, GQ, Xq, w.ld, w.terms, nullptr, n, st, 0.0f, &st->gmax_next, s);
+        // the LOT direction enters the step size and the update in FP32, recomputed from
+        // its duals (the products took it rounded); FAQ's permutation is exact in Xq
+        const float *fq = faq ? nullptr : f, *gq = faq ? nullptr : g;
+        line_search(G, GQ, P, Xq, w.ld, w.terms, nullptr, fq, gq, n, partial, st, s);
+        fw_update(P, G, GQ, Xq, w.ld, w.terms, nullptr, fq, gq, n, st, 0.0f, &st->gmax_next, s);
         fw_roll(st, s);
         if (prof) cudaEventRecord(pe[5], s);
         GOAT_TRY(cuda_status(cudaMemcpyAsync(pinned, &st->fw_done, sizeof(int), cudaMemcpyDeviceToHost, s)));
@@ -711,7 +740,10 @@ static goat_params resolve_params(const goat_params *p) {
     return r;
 }
 
-static bool valid_precision(int p) { return p == GOAT_PREC_BF16 || p == GOAT_PREC_FP32 || p == GOAT_PREC_FP8; }
+static bool valid_precision(int p) {
+    return p == GOAT_PREC_BF16 || p == GOAT_PREC_FP32 || p == GOAT_PREC_FP8 || p == GOAT_PREC_BF16_SPLIT ||
+           p == GOAT_PREC_FP8_SPLIT;
+}
 
 // The solve's shape from its parameters; false if they do not fit n.
 static bool match_shape(const goat_params &p, int n, Shape *sh) {
@@ -896,7 +928,7 @@ int goat_line_search(const float *G, const float *G_Q, const float *P, const flo
     GOAT_TRY(ws.acquire(workspace, workspace_bytes, w.total, s));
     DevState *st = ws.at<DevState>(w.state);
     GOAT_TRY(init_state(st, 0.03f, maximize ? 1 : 0, 0.0f, s));
-    line_search(G, G_Q, P, nullptr, 0, 1, Q, n, ws.at<double>(w.partial), st, s);
+    line_search(G, G_Q, P, nullptr, 0, 1, Q, nullptr, nullptr, n, ws.at<double>(w.partial), st, s);
     DevState hs;
     GOAT_TRY(cuda_status(cudaMemcpyAsync(&hs, st, offsetof(DevState, tr_sk_iters), cudaMemcpyDeviceToHost, s)));
     GOAT_TRY(cuda_status(cudaStreamSynchronize(s)));
@@ -910,7 +942,7 @@ int goat_fw_update(float *P, float *G, const float *Q, const float *G_Q, int n, 
     if (!P || !G || !Q || !G_Q || n < 1 || !(alpha >= 0.0 && alpha <= 1.0)) return GOAT_ERR_INVALID_ARG;
     GOAT_TRY(device_ok());
     cudaStream_t s = (cudaStream_t)stream;
-    fw_update(P, G, G_Q, nullptr, 0, 1, Q, n, nullptr, (float)alpha, nullptr, s);
+    fw_update(P, G, G_Q, nullptr, 0, 1, Q, nullptr, nullptr, n, nullptr, (float)alpha, nullptr, s);
     return cuda_status(cudaGetLastError());
 }
 

@@ -322,6 +322,24 @@ __device__ __forceinline__ LsQuad ls_load(const float *__restrict__ G, const flo
     return u;
 }
 
+// The same four columns with Q recomputed in FP32 from the LOT duals,
+// Q_ij = 2^(c (f_i + g_j - G_ij)) -- the expression (and so the value) the Q writer
+// rounds for the products -- instead of read back from the products' BF16 operand.
+__device__ __forceinline__ LsQuad ls_load_dual(const float *__restrict__ G, const float *__restrict__ GQ,
+                                               const float *__restrict__ P, float fi, const float *__restrict__ g,
+                                               float c, long long base, int j) {
+    LsQuad u;
+    u.g = *reinterpret_cast<const float4 *>(G + base + j);
+    u.h = *reinterpret_cast<const float4 *>(GQ + base + j);
+    u.p = *reinterpret_cast<const float4 *>(P + base + j);
+    const float4 gj = __ldg(reinterpret_cast<const float4 *>(g + j));
+    u.q[0] = fast_exp2((fi + gj.x - u.g.x) * c);
+    u.q[1] = fast_exp2((fi + gj.y - u.g.y) * c);
+    u.q[2] = fast_exp2((fi + gj.z - u.g.z) * c);
+    u.q[3] = fast_exp2((fi + gj.w - u.g.w) * c);
+    return u;
+}
+
 __device__ __forceinline__ void ls_accumulate(const LsQuad &u, float &a1, float &a2, float &a3) {
     const float d0 = u.q[0] - u.p.x, d1 = u.q[1] - u.p.y, d2 = u.q[2] - u.p.z, d3 = u.q[3] - u.p.w;
     a1 += u.g.x * d0 + u.g.y * d1 + u.g.z * d2 + u.g.w * d3;
@@ -330,35 +348,51 @@ __device__ __forceinline__ void ls_accumulate(const LsQuad &u, float &a1, float 
 }
 
 // Per-block partial sums of <G, D>, <G_Q, D>, <D, D> with D = Q - P, where Q is
-// given either as BF16 split terms (the exact values the GEMMs consumed) or as
+// recomputed in FP32 from the LOT duals (f, g non-null: the value the Sinkhorn step
+// defines, unrounded), or given as BF16 split terms (FAQ's permutation, exact) or as
 // FP32.  One block per row at a time; FP32 within a row segment, FP64 across.
 __global__ void __launch_bounds__(256) k_ls_partial(const float *__restrict__ G, const float *__restrict__ GQ,
                                                     const float *__restrict__ P, const __nv_bfloat16 *__restrict__ Qb,
-                                                    int ldq, int terms, const float *__restrict__ Qf, int n,
-                                                    double *__restrict__ out) {
+                                                    int ldq, int terms, const float *__restrict__ Qf,
+                                                    const float *__restrict__ fd, const float *__restrict__ gd,
+                                                    const DevState *__restrict__ st, int n, double *__restrict__ out) {
     double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    const bool dual = fd != nullptr;
+    const float c = dual ? st->c : 0.0f;
     const bool vec = ((n & 3) == 0) && (Qf == nullptr) &&
                      (((reinterpret_cast<uintptr_t>(G) | reinterpret_cast<uintptr_t>(GQ) |
-                        reinterpret_cast<uintptr_t>(P)) & 15) == 0);
+                        reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(gd)) & 15) == 0);
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
         const long long base = (long long)i * n;
         const __nv_bfloat16 *qrow = Qb ? Qb + (long long)i * ((long long)terms * ldq) : nullptr;
+        const float fi = dual ? __ldg(fd + i) : 0.0f;
         float a1 = 0.f, a2 = 0.f, a3 = 0.f;
         if (vec) {
             // two steps' loads in flight before either is accumulated; the terms
             // are still added in the order of j
             const int step = blockDim.x * 4;
             int j = threadIdx.x * 4;
-            for (; j + step < n; j += 2 * step) {
-                const LsQuad u = ls_load(G, GQ, P, qrow, ldq, terms, base, j);
-                const LsQuad v = ls_load(G, GQ, P, qrow, ldq, terms, base, j + step);
-                ls_accumulate(u, a1, a2, a3);
-                ls_accumulate(v, a1, a2, a3);
+            if (dual) {
+                for (; j + step < n; j += 2 * step) {
+                    const LsQuad u = ls_load_dual(G, GQ, P, fi, gd, c, base, j);
+                    const LsQuad v = ls_load_dual(G, GQ, P, fi, gd, c, base, j + step);
+                    ls_accumulate(u, a1, a2, a3);
+                    ls_accumulate(v, a1, a2, a3);
+                }
+                if (j < n) ls_accumulate(ls_load_dual(G, GQ, P, fi, gd, c, base, j), a1, a2, a3);
+            } else {
+                for (; j + step < n; j += 2 * step) {
+                    const LsQuad u = ls_load(G, GQ, P, qrow, ldq, terms, base, j);
+                    const LsQuad v = ls_load(G, GQ, P, qrow, ldq, terms, base, j + step);
+                    ls_accumulate(u, a1, a2, a3);
+                    ls_accumulate(v, a1, a2, a3);
+                }
+                if (j < n) ls_accumulate(ls_load(G, GQ, P, qrow, ldq, terms, base, j), a1, a2, a3);
             }
-            if (j < n) ls_accumulate(ls_load(G, GQ, P, qrow, ldq, terms, base, j), a1, a2, a3);
         } else {
             for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                const float q = Qf ? Qf[base + j] : q_terms(qrow, ldq, terms, j);
+                const float q = dual ? fast_exp2((fi + __ldg(gd + j) - G[base + j]) * c)
+                                     : (Qf ? Qf[base + j] : q_terms(qrow, ldq, terms, j));
                 const float d = q - P[base + j];
                 a1 = fmaf(G[base + j], d, a1);
                 a2 = fmaf(GQ[base + j], d, a2);
@@ -446,30 +480,40 @@ __global__ void k_ls_final(const double *__restrict__ part, int nblocks, int n, 
 // P <- P + alpha (Q - P), G <- G + alpha (G_Q - G); accumulates max|G_new|.
 __global__ void __launch_bounds__(256) k_fw_update(float *__restrict__ P, float *__restrict__ G,
                                                    const float *__restrict__ GQ, const __nv_bfloat16 *__restrict__ Qb,
-                                                   int ldq, int terms, const float *__restrict__ Qf, int n,
+                                                   int ldq, int terms, const float *__restrict__ Qf,
+                                                   const float *__restrict__ fd, const float *__restrict__ gd, int n,
                                                    const DevState *__restrict__ st, float alpha_value,
                                                    unsigned *gmax_out) {
     const float alpha = st ? (float)st->alpha : alpha_value;
+    const bool dual = fd != nullptr;  // Q from the LOT duals and the G before the update
+    const float c = dual ? st->c : 0.0f;
     float gm = 0.0f;
     const bool vec = ((n & 3) == 0) && (Qf == nullptr) &&
                      (((reinterpret_cast<uintptr_t>(G) | reinterpret_cast<uintptr_t>(GQ) |
-                        reinterpret_cast<uintptr_t>(P)) & 15) == 0);
+                        reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(gd)) & 15) == 0);
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
         const long long base = (long long)i * n;
         const __nv_bfloat16 *qrow = Qb ? Qb + (long long)i * ((long long)terms * ldq) : nullptr;
+        const float fi = dual ? __ldg(fd + i) : 0.0f;
         if (vec) {
             for (int j = threadIdx.x * 4; j < n; j += blockDim.x * 4) {
                 float4 p4 = *reinterpret_cast<const float4 *>(P + base + j);
                 float4 g4 = *reinterpret_cast<const float4 *>(G + base + j);
                 const float4 h4 = *reinterpret_cast<const float4 *>(GQ + base + j);
-                const uint2 qh = *reinterpret_cast<const uint2 *>(qrow + j);
                 float q[4];
-                {
+                if (dual) {
+                    const float4 gj = __ldg(reinterpret_cast<const float4 *>(gd + j));
+                    q[0] = fast_exp2((fi + gj.x - g4.x) * c);
+                    q[1] = fast_exp2((fi + gj.y - g4.y) * c);
+                    q[2] = fast_exp2((fi + gj.z - g4.z) * c);
+                    q[3] = fast_exp2((fi + gj.w - g4.w) * c);
+                } else {
+                    const uint2 qh = *reinterpret_cast<const uint2 *>(qrow + j);
                     const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&qh.x));
                     const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&qh.y));
                     q[0] = lo.x; q[1] = lo.y; q[2] = hi.x; q[3] = hi.y;
                 }
-                if (terms > 1) {
+                if (!dual && terms > 1) {
                     const uint2 ql = *reinterpret_cast<const uint2 *>(qrow + ldq + j);
                     const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&ql.x));
                     const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&ql.y));
@@ -489,8 +533,9 @@ __global__ void __launch_bounds__(256) k_fw_update(float *__restrict__ P, float 
             }
         } else {
             for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                const float q = Qf ? Qf[base + j] : q_terms(qrow, ldq, terms, j);
                 const float p = P[base + j], g = G[base + j];
+                const float q = dual ? fast_exp2((fi + __ldg(gd + j) - g) * c)
+                                     : (Qf ? Qf[base + j] : q_terms(qrow, ldq, terms, j));
                 P[base + j] = fmaf(alpha, q - p, p);
                 const float gn = fmaf(alpha, GQ[base + j] - g, g);
                 G[base + j] = gn;
@@ -830,17 +875,19 @@ int write_perm_q(const int32_t *perm, int n, __nv_bfloat16 *Qb, int ldq, int ter
 int ls_blocks(int n) { return rows_grid(n, 4); }
 
 void line_search(const float *G, const float *GQ, const float *P, const __nv_bfloat16 *Qb, int ldq, int terms,
-                 const float *Qf, int n, double *partial, DevState *st, cudaStream_t s) {
+                 const float *Qf, const float *f, const float *g, int n, double *partial, DevState *st,
+                 cudaStream_t s) {
     note_launches(2);
     const int nb = ls_blocks(n);
-    k_ls_partial<<<nb, 256, 0, s>>>(G, GQ, P, Qb, ldq, terms, Qf, n, partial);
+    k_ls_partial<<<nb, 256, 0, s>>>(G, GQ, P, Qb, ldq, terms, Qf, f, g, st, n, partial);
     k_ls_final<<<1, 32, 0, s>>>(partial, nb, n, st);
 }
 
 void fw_update(float *P, float *G, const float *GQ, const __nv_bfloat16 *Qb, int ldq, int terms, const float *Qf,
-               int n, const DevState *st, float alpha_value, unsigned *gmax_out, cudaStream_t s) {
+               const float *f, const float *g, int n, const DevState *st, float alpha_value, unsigned *gmax_out,
+               cudaStream_t s) {
     note_launches(1);
-    k_fw_update<<<rows_grid(n), 256, 0, s>>>(P, G, GQ, Qb, ldq, terms, Qf, n, st, alpha_value, gmax_out);
+    k_fw_update<<<rows_grid(n), 256, 0, s>>>(P, G, GQ, Qb, ldq, terms, Qf, f, g, n, st, alpha_value, gmax_out);
 }
 
 void fw_roll(DevState *st, cudaStream_t s) { k_fw_roll<<<1, 1, 0, s>>>(st); }

@@ -114,10 +114,15 @@ void seed_perm(int32_t *perm, int n, int m, cudaStream_t s);
 void embed_block(const float *P22, int n, int m, float *out, cudaStream_t s);
 void absmax(const float *X, long long total, unsigned *out, cudaStream_t s);
 int ls_blocks(int n);
+// Q for the step size and the update: from the LOT duals f, g (non-null: recomputed
+// in FP32 from G, Q_ij = 2^(c (f_i + g_j - G_ij)) with st->c), else the BF16 split
+// terms Qb, else FP32 Qf.
 void line_search(const float *G, const float *GQ, const float *P, const __nv_bfloat16 *Qb, int ldq, int terms,
-                 const float *Qf, int n, double *partial, DevState *st, cudaStream_t s);
+                 const float *Qf, const float *f, const float *g, int n, double *partial, DevState *st,
+                 cudaStream_t s);
 void fw_update(float *P, float *G, const float *GQ, const __nv_bfloat16 *Qb, int ldq, int terms, const float *Qf,
-               int n, const DevState *st, float alpha_value, unsigned *gmax_out, cudaStream_t s);
+               const float *f, const float *g, int n, const DevState *st, float alpha_value, unsigned *gmax_out,
+               cudaStream_t s);
 void fw_roll(DevState *st, cudaStream_t s);
 // Blocks of the FP64 objective sums (a fixed grid, so the sums are reproducible);
 // objective() takes 3 * kObjBlocks doubles of scratch in fpart, and fsum, fA, fB
