@@ -133,6 +133,10 @@ int objective(const void *A, const void *B, int dtype, int n, const int32_t *per
               double *fpart, cudaStream_t s);
 
 // goat_sinkhorn.cu
+// Smallest n the fused single-read Sinkhorn iteration runs at (below it the row and
+// column passes run, which are faster there: the fused form's cost per row is
+// mostly fixed); sinkhorn_partial_elems covers both.
+constexpr int kSkFusedMinN = 24576;
 long long sinkhorn_partial_elems(int n);
 void sinkhorn_begin(DevState *st, float eps, float tol, float *g_zero, int n, cudaStream_t s);
 int sinkhorn_solve(const float *G, int n, long long ld, float *f, float *g, double *partial, DevState *st,

@@ -25,6 +25,8 @@ constexpr size_t kNoallocStateBytes = 16384;
 constexpr size_t kNoallocScratchBytes = kNoallocStateBytes + (size_t)(kNoallocMaxN / 64) * kNoallocMaxN * 8;
 
 static_assert(sizeof(DevState) <= kNoallocStateBytes, "state block does not fit its slot");
+// the partial sums above are laid out for the two-pass iteration (ceil(n / 64) row chunks)
+static_assert(kNoallocMaxN < kSkFusedMinN, "the fused iteration's partial sums need more room");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 

@@ -291,6 +291,261 @@ __global__ void k_sk_begin(DevState *st, float eps, float tol, float *g_zero, in
         for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) g_zero[j] = 0.0f;
 }
 
+// ---------------------------------------------------------------- fused iteration
+
+// One Sinkhorn iteration in a single read of G (kSkFusedMinN <= n <= 32768, n a
+// multiple of 16, G dense and 16-byte aligned), for every iteration of a solve after
+// its first.  A cluster of four CTAs takes whole rows; CTA h holds the columns
+// [h W, h W + W), W = n / 4, of each row, streamed from HBM into a ring of five
+// shared-memory buffers by 1-D bulk copies (issued by a control warp).
+//
+// The previous iteration's row duals f' stabilise the exponents: its column scaling
+// made every column of exp((f'_i + g_j - G_ij)/eps) sum to exactly 1, so each term
+// is at most 1 and each row sums to at least 1/n -- no maximum is needed.  For row t
+// each compute thread forms e_j = 2^(c (f'_t + g_j - G_tj)) for its 16 columns (one
+// exp2 per element), keeps them in registers and sums them; the control warp adds the
+// warps' sums in warp order, frees the row's buffer for the next copy and stores the
+// CTA's sum, asynchronously through distributed shared memory, into the other three
+// CTAs.  Two rows later (so the exchange's latency hides behind two rows of work)
+// the four sums are added in rank order into the row sum S (the same bits in every
+// CTA), f_t = f'_t - log2(S) / c, and the row-scaled entries Q_tj = e_j / S go into
+// the thread's column sums (FP32 over groups of 16 rows, whose sums are added in
+// FP32 in shared memory, written as FP64 per cluster for k_sk_colfinal).  Shared memory sees each
+// entry twice (the copy in, one read).  Every wait is bounded; on expiry the CTA
+// drains its copies, meets the other CTAs and reports GOAT_ERR_TIMEOUT.
+constexpr int kSkFusedThreads = 512;  // 16 compute warps; a 17th warp is the control warp
+constexpr int kSkCluster = 4;
+constexpr int kSkBuffers = 5;
+// Rows in the exchange ring: a CTA stores its pair of row t + 8 only after it has
+// received every CTA's pair of row t + 7, so the stores of row t have seven rows of
+// work to land before their slot comes round again.
+constexpr int kSkSlots = 8;
+// A row's entries go into the column sums kSkDefer rows after its exponents (the
+// exchange's latency hides behind that much work); the exponents wait in registers.
+constexpr int kSkDefer = 2;
+// Rows one cluster may take: their f' are staged in shared memory at the start.
+constexpr int kSkMaxRows = 1024;
+
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+// A float into another CTA's shared memory, completing 4 transaction bytes on that
+// CTA's barrier (asynchronous: the sender does not wait for it).
+__device__ __forceinline__ void st_async_f32(uint32_t remote_addr, float a, uint32_t remote_bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];" ::"r"(remote_addr),
+                 "f"(a), "r"(remote_bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_load_1d(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Bounded wait on a barrier phase that ignores the abort flag (draining copies).
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = global_timer_ns();
+    while (!mbar_try_wait(bar, parity) && global_timer_ns() - t0 < 200000000ull) {
+    }
+}
+
+// Row t of a compute thread: e_q = 2^(c (f'_t + g_j - G_tj)) <= 1 for its columns
+// j = 4 (tid + 512 v) + k, q = 4 v + k (float4 reads of the row in shared memory),
+// kept in registers, and their sum.
+template <int CPT>
+__device__ __forceinline__ void fused_row_exp(const float *__restrict__ rowbuf, int W, int tid, float c, float cf,
+                                              const float (&gc)[CPT], float (&e)[CPT], float &sum) {
+    sum = 0.0f;
+    const float4 *row4 = reinterpret_cast<const float4 *>(rowbuf);
+#pragma unroll
+    for (int v = 0; v < CPT / 4; ++v) {
+        const int j4 = tid + v * kSkFusedThreads;
+        if (4 * j4 < W) {
+            const float4 x = row4[j4];
+            e[4 * v + 0] = fast_exp2(fmaf(x.x, -c, gc[4 * v + 0] + cf));
+            e[4 * v + 1] = fast_exp2(fmaf(x.y, -c, gc[4 * v + 1] + cf));
+            e[4 * v + 2] = fast_exp2(fmaf(x.z, -c, gc[4 * v + 2] + cf));
+            e[4 * v + 3] = fast_exp2(fmaf(x.w, -c, gc[4 * v + 3] + cf));
+            sum += (e[4 * v + 0] + e[4 * v + 1]) + (e[4 * v + 2] + e[4 * v + 3]);
+        } else {
+            e[4 * v + 0] = e[4 * v + 1] = e[4 * v + 2] = e[4 * v + 3] = 0.0f;
+        }
+    }
+}
+
+template <int CPT>
+__global__ void __cluster_dims__(kSkCluster, 1, 1) __launch_bounds__(kSkFusedThreads + 32, 1)
+    k_sk_fused(const float *__restrict__ G, int n, const float *__restrict__ g, float *__restrict__ f,
+               double *__restrict__ partial, DevState *st) {
+    static_assert(CPT % 4 == 0 && kSkDefer == 2, "float4 columns; two register sets of deferred rows");
+    if (st->sk_done) return;  // uniform over the cluster: every CTA reads the same flag
+    extern __shared__ __align__(128) unsigned char sk_smem[];
+    constexpr int NW = kSkFusedThreads / 32;  // compute warps; warp NW is the control warp
+    const int W = n / kSkCluster;
+    float *bufs = reinterpret_cast<float *>(sk_smem);  // kSkBuffers rows of W floats
+    // the sums of whole groups of 16 rows, column q of thread tid at [q][tid]
+    float *grp = bufs + (size_t)kSkBuffers * W;
+    __shared__ __align__(8) uint64_t full_bar[kSkBuffers], sums_bar[kSkSlots], xch_bar[kSkSlots];
+    __shared__ __align__(8) float xch[kSkSlots][kSkCluster];  // the cluster's row sums, slot = row mod 8
+    __shared__ float red[kSkSlots][NW];                        // the compute warps' sums, slot = row mod 8
+    __shared__ float f_stage[kSkMaxRows];                      // f' of this cluster's rows
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t rank = cluster_rank();
+    const int cid = blockIdx.x / kSkCluster, ncl = gridDim.x / kSkCluster;
+    const int col0 = (int)rank * W;
+    const int K = cid < n ? (n - 1 - cid) / ncl + 1 : 0;  // rows of this cluster: cid + t ncl
+    const uint32_t bytes = (uint32_t)W * 4u;
+
+    if (tid == 0) {
+        for (int b = 0; b < kSkBuffers; ++b) mbar_init(smem_u32(&full_bar[b]), 1);
+        for (int b = 0; b < kSkSlots; ++b) {
+            mbar_init(smem_u32(&sums_bar[b]), NW);
+            // a row's exchange completes with this CTA's own sum (one arrival, which also
+            // expects the other CTAs' bytes) and the 3 x 4 bytes they store asynchronously
+            mbar_init(smem_u32(&xch_bar[b]), 1);
+        }
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    const float c = st->c;
+    for (int t = tid; t < K; t += blockDim.x) f_stage[t] = f[cid + t * ncl];
+    __syncthreads();
+    cluster_sync_all();  // every CTA's barriers exist before any remote store
+    volatile int *abort = &abort_flag;
+    const uint32_t xch_base = smem_u32(&xch[0][0]), xbar_base = smem_u32(&xch_bar[0]);
+    auto issue = [&](int t) {  // the copy of row t into its ring slot
+        const int b = t % kSkBuffers;
+        const uint32_t bar = smem_u32(&full_bar[b]);
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_load_1d(smem_u32(bufs + (size_t)b * W), G + (size_t)(cid + t * ncl) * n + col0, bytes, bar);
+    };
+    // bounded wait for a phase; false (and the abort flag raised) on expiry or abort
+    auto wait = [&](uint32_t bar, uint32_t parity) -> bool { return mbar_wait_bounded(bar, parity, abort); };
+
+    int issued = K < kSkBuffers ? K : kSkBuffers;
+    if (warp == NW) {
+        // ---------------- control warp: the CTA's row sums, the exchange, the copies
+        if (lane == 0) {
+            for (int t = 0; t < issued; ++t) issue(t);
+            for (int t = 0; t < K; ++t) {
+                const int slot = t % kSkSlots;
+                if (!wait(smem_u32(&sums_bar[slot]), (uint32_t)(t / kSkSlots) & 1u)) break;
+                float cs = 0.0f;
+                for (int w = 0; w < NW; ++w) cs += red[slot][w];  // warp order: fixed
+                const uint32_t off = 4u * (uint32_t)(slot * kSkCluster + (int)rank);
+                xch[slot][rank] = cs;
+                mbar_arrive_expect_tx(xbar_base + 8u * (uint32_t)slot, 4u * (kSkCluster - 1));
+                for (int r = 0; r < kSkCluster; ++r) {
+                    if (r == (int)rank) continue;
+                    st_async_f32(mapa_shared(xch_base, r) + off, cs, mapa_shared(xbar_base, r) + 8u * (uint32_t)slot);
+                }
+                // every compute warp has read row t (its exponents are in registers):
+                // its buffer takes row t + kSkBuffers
+                if (issued < K) issue(issued++);
+            }
+        }
+    } else {
+        // ---------------- compute warps
+        float gc[CPT];  // c g_j
+#pragma unroll
+        for (int v = 0; v < CPT / 4; ++v) {
+            const int j = 4 * (tid + v * kSkFusedThreads);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) gc[4 * v + k] = j < W ? g[col0 + j + k] * c : 0.0f;
+        }
+        float acc[CPT], e0[CPT], e1[CPT];
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            acc[q] = 0.0f;
+            grp[q * kSkFusedThreads + tid] = 0.0f;
+        }
+        // row t's exponents and their sum (false on abort)
+        auto row_exp = [&](int t, float (&e)[CPT]) -> bool {
+            const int b = t % kSkBuffers;
+            const float cf = c * f_stage[t];
+            if (!wait(smem_u32(&full_bar[b]), (uint32_t)(t / kSkBuffers) & 1u)) return false;
+            float sum;
+            fused_row_exp<CPT>(bufs + (size_t)b * W, W, tid, c, cf, gc, e, sum);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (lane == 0) {
+                red[t % kSkSlots][warp] = sum;
+                mbar_arrive(smem_u32(&sums_bar[t % kSkSlots]));  // also: this warp is done with the buffer
+            }
+            return true;
+        };
+        // row tp's cluster sum S, f_tp, and its entries e / S into the column sums
+        auto row_acc = [&](int tp, const float (&e)[CPT]) -> bool {
+            const int slot = tp % kSkSlots;
+            if (!wait(xbar_base + 8u * (uint32_t)slot, (uint32_t)(tp / kSkSlots) & 1u)) return false;
+            // rank order: the same bits in every CTA of the cluster
+            float S = xch[slot][0];
+#pragma unroll
+            for (int r = 1; r < kSkCluster; ++r) S += xch[slot][r];
+            if (rank == 0 && tid == 0) f[cid + tp * ncl] = f_stage[tp] - __log2f(S) / c;
+            const float scale = 1.0f / S;
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) acc[q] = fmaf(e[q], scale, acc[q]);
+            if ((tp & 15) == 15) {
+#pragma unroll
+                for (int q = 0; q < CPT; ++q) {
+                    grp[q * kSkFusedThreads + tid] += acc[q];
+                    acc[q] = 0.0f;
+                }
+            }
+            return true;
+        };
+        // row t's exponents go into set t mod 2; that set is first freed by adding row
+        // t - 2 (kSkDefer) into the column sums
+        bool ok = true;
+        for (int t = 0; ok && t < K + kSkDefer; t += 2) {
+            if (t >= 2) ok = row_acc(t - 2, e0);
+            if (ok && t < K) ok = row_exp(t, e0);
+            if (ok && t >= 1 && t - 1 < K) ok = row_acc(t - 1, e1);
+            if (ok && t + 1 < K) ok = row_exp(t + 1, e1);
+        }
+        if (ok && !*abort) {
+            double *dst = partial + (size_t)cid * n + col0;
+#pragma unroll
+            for (int v = 0; v < CPT / 4; ++v) {
+                const int j = 4 * (tid + v * kSkFusedThreads);
+                if (j < W) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        dst[j + k] = (double)grp[(4 * v + k) * kSkFusedThreads + tid] + (double)acc[4 * v + k];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const bool aborted = *abort != 0;
+    if (aborted && warp == NW && lane == 0) {
+        // let the copies in flight land before the shared memory is released (the last
+        // kSkBuffers issued rows, one per buffer)
+        for (int tt = issued > kSkBuffers ? issued - kSkBuffers : 0; tt < issued; ++tt)
+            mbar_drain(smem_u32(&full_bar[tt % kSkBuffers]), (uint32_t)(tt / kSkBuffers) & 1u);
+    }
+    __syncthreads();
+    cluster_sync_all();  // no CTA leaves while another may still write into it
+    if (aborted && tid == 0 && !st->error) st->error = GOAT_ERR_TIMEOUT;
+}
+
 // ---------------------------------------------------------------- Q materialisation
 
 // Q_ij = 2^(c (f_i + g_j - G_ij)), written as BF16 split terms (hi, and lo when
@@ -392,9 +647,80 @@ static SinkhornLaunch sinkhorn_launch(int n) {
     return L;
 }
 
+// Clusters of the fused iteration: at most one CTA per SM (the bound the partial-sum
+// buffer is sized for); the launch uses as many as are co-resident.
+static int fused_clusters() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(1, sms / kSkCluster);
+}
+
+// Clusters of k_sk_fused<CPT> that fit on the device at once with `smem` bytes each:
+// the rows are spread over exactly one wave of them (a cluster must sit within one
+// GPC, so fewer pairs than SMs / 2 may be co-resident, and a second, partial wave
+// would double the pass).  Cached per instantiation and size.
+template <typename Kern>
+static int fused_wave_clusters(Kern kern, size_t smem) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kSkCluster * fused_clusters());
+    cfg.blockDim = dim3(kSkFusedThreads + 32);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = kSkCluster;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, (const void *)kern, &cfg) != cudaSuccess || ncl < 1) {
+        cudaGetLastError();
+        ncl = fused_clusters();
+    }
+    return std::min(ncl, fused_clusters());
+}
+
+static bool use_fused(const float *G, int n, long long ld) {
+    return n >= kSkFusedMinN && n <= kSkCluster * kSkFusedThreads * 16 && (n % 16) == 0 && ld == n &&
+           (reinterpret_cast<uintptr_t>(G) & 15) == 0;
+}
+
 long long sinkhorn_partial_elems(int n) {
     SinkhornLaunch L = sinkhorn_launch(n);
-    return (long long)L.colpart_y * n;
+    const long long chunks = n >= kSkFusedMinN ? std::max<long long>(L.colpart_y, fused_clusters()) : L.colpart_y;
+    return chunks * n;
+}
+
+// Queues the fused iteration (k_sk_fused + k_sk_colfinal over the clusters' partial
+// column sums); returns false if its launch could not be configured.
+static bool sinkhorn_fused(const float *G, int n, float *f, float *g, double *partial, DevState *st,
+                           cudaStream_t s) {
+    const int W = n / kSkCluster;
+    const size_t smem = ((size_t)kSkBuffers * W + (size_t)16 * kSkFusedThreads) * sizeof(float);
+    // n >= kSkFusedMinN: W > 4096 columns, at most 16 a thread.  The kernel is
+    // configured once for the largest quarter-row it takes (W = 512 * 16); the
+    // clusters that fit in one wave are found once per n.
+    auto kern = k_sk_fused<16>;
+    static bool configured = false;
+    static int wave_n = 0, wave_ncl = 0;
+    if (!configured) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (kSkBuffers + 1) * kSkFusedThreads * 16 * (int)sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        configured = true;
+    }
+    if (wave_n != n) {
+        wave_ncl = fused_wave_clusters(kern, smem);
+        wave_n = n;
+    }
+    const int ncl = wave_ncl;
+    if (ceil_div(n, ncl) > kSkMaxRows) return false;  // more rows a cluster than f' slots
+    kern<<<kSkCluster * ncl, kSkFusedThreads + 32, smem, s>>>(G, n, g, f, partial, st);
+    k_sk_colfinal<<<(int)ceil_div(n, 256), 256, 0, s>>>(partial, ncl, n, G, n, f, g, st);
+    return true;
 }
 
 // Queues the column pass: full, aligned 2048-column CTAs take the fallback-free
@@ -413,12 +739,18 @@ static int sinkhorn_colpart(const float *G, int n, long long ld, const float *f,
     return (full > 0) + (edge > 0);
 }
 
-// Queues one Sinkhorn iteration.
+// Queues one Sinkhorn iteration: the fused single-read form where it applies (G
+// read once, 4 n^2 bytes), else the row pass and the column pass (G read twice).
 static void sinkhorn_iteration(const float *G, int n, long long ld, float *f, float *g, double *partial,
-                               DevState *st, int max_iter, const SinkhornLaunch &L, cudaStream_t s) {
-    k_sk_row<<<L.row_grid, 256, 0, s>>>(G, n, ld, g, f, st);
-    note_launches(3 + sinkhorn_colpart(G, n, ld, f, g, partial, st, L, s));
-    k_sk_colfinal<<<L.final_grid, 256, 0, s>>>(partial, L.colpart_y, n, G, ld, f, g, st);
+                               DevState *st, int max_iter, const SinkhornLaunch &L, bool first, cudaStream_t s) {
+    // the fused form takes the previous iteration's f as its stabiliser: not on the first
+    if (!first && use_fused(G, n, ld) && sinkhorn_fused(G, n, f, g, partial, st, s)) {
+        note_launches(3);
+    } else {
+        k_sk_row<<<L.row_grid, 256, 0, s>>>(G, n, ld, g, f, st);
+        note_launches(3 + sinkhorn_colpart(G, n, ld, f, g, partial, st, L, s));
+        k_sk_colfinal<<<L.final_grid, 256, 0, s>>>(partial, L.colpart_y, n, G, ld, f, g, st);
+    }
     k_sk_check<<<1, 1, 0, s>>>(st, max_iter);
 }
 
@@ -432,7 +764,7 @@ int sinkhorn_solve(const float *G, int n, long long ld, float *f, float *g, doub
     int done_iters = 0;
     while (done_iters < max_iter) {
         const int k = std::min(check_every, max_iter - done_iters);
-        for (int t = 0; t < k; ++t) sinkhorn_iteration(G, n, ld, f, g, partial, st, max_iter, L, s);
+        for (int t = 0; t < k; ++t) sinkhorn_iteration(G, n, ld, f, g, partial, st, max_iter, L, done_iters + t == 0, s);
         done_iters += k;
         if (cudaMemcpyAsync(host_flag, &st->sk_done, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return GOAT_ERR_CUDA;
@@ -447,7 +779,7 @@ int sinkhorn_solve(const float *G, int n, long long ld, float *f, float *g, doub
 void sinkhorn_queue_fixed(const float *G, int n, long long ld, float *f, float *g, double *partial, DevState *st,
                           int max_iter, cudaStream_t s) {
     const SinkhornLaunch L = sinkhorn_launch(n);
-    for (int t = 0; t < max_iter; ++t) sinkhorn_iteration(G, n, ld, f, g, partial, st, max_iter, L, s);
+    for (int t = 0; t < max_iter; ++t) sinkhorn_iteration(G, n, ld, f, g, partial, st, max_iter, L, t == 0, s);
 }
 
 void sinkhorn_begin(DevState *st, float eps, float tol, float *g_zero, int n, cudaStream_t s) {
