@@ -136,7 +136,7 @@ int objective(const void *A, const void *B, int dtype, int n, const int32_t *per
 // Smallest n the fused single-read Sinkhorn iteration runs at (below it the row and
 // column passes run, which are faster there: the fused form's cost per row is
 // mostly fixed); sinkhorn_partial_elems covers both.
-constexpr int kSkFusedMinN = 24576;
+constexpr int kSkFusedMinN = 20480;
 long long sinkhorn_partial_elems(int n);
 void sinkhorn_begin(DevState *st, float eps, float tol, float *g_zero, int n, cudaStream_t s);
 int sinkhorn_solve(const float *G, int n, long long ld, float *f, float *g, double *partial, DevState *st,
@@ -170,6 +170,8 @@ struct LapControl {
     long long tail_stall;  // bids without the queue shrinking that end the Gauss-Seidel tail
     long long sap_pops;    // row scans the augmenting-path searches may do per phase (0: none)
     int sap_step;          // columns a search settles per parallel step
+    int head_stall;        // Jacobi rounds without fewer bidders that end a phase's rounds
+    int sap_every_phase;   // 1: the searches complete every phase; 0: only the last
 };
 void lap_default_control(LapControl *c);
 struct LapReport {

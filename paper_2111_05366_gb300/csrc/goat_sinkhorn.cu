@@ -306,10 +306,11 @@ __global__ void k_sk_begin(DevState *st, float eps, float tol, float *g_zero, in
 // exp2 per element), keeps them in registers and sums them; the control warp adds the
 // warps' sums in warp order, frees the row's buffer for the next copy and stores the
 // CTA's sum, asynchronously through distributed shared memory, into the other three
-// CTAs.  Two rows later (so the exchange's latency hides behind two rows of work)
-// the four sums are added in rank order into the row sum S (the same bits in every
-// CTA), f_t = f'_t - log2(S) / c, and the row-scaled entries Q_tj = e_j / S go into
-// the thread's column sums (FP32 over groups of 16 rows, whose sums are added in
+// CTAs.  A row later (so the exchange's latency hides behind a row of work) the
+// control warp adds the four sums in rank order into the row sum S (the same bits
+// in every CTA), writes f_t = f'_t - log2(S) / c and publishes 1 / S; a row after
+// that the compute warps add the row-scaled entries Q_tj = e_j / S into the
+// thread's column sums (FP32 over groups of 16 rows, whose sums are added in
 // FP32 in shared memory, written as FP64 per cluster for k_sk_colfinal).  Shared memory sees each
 // entry twice (the copy in, one read).  Every wait is bounded; on expiry the CTA
 // drains its copies, meets the other CTAs and reports GOAT_ERR_TIMEOUT.
@@ -399,9 +400,10 @@ __global__ void __cluster_dims__(kSkCluster, 1, 1) __launch_bounds__(kSkFusedThr
     float *bufs = reinterpret_cast<float *>(sk_smem);  // kSkBuffers rows of W floats
     // the sums of whole groups of 16 rows, column q of thread tid at [q][tid]
     float *grp = bufs + (size_t)kSkBuffers * W;
-    __shared__ __align__(8) uint64_t full_bar[kSkBuffers], sums_bar[kSkSlots], xch_bar[kSkSlots];
+    __shared__ __align__(8) uint64_t full_bar[kSkBuffers], sums_bar[kSkSlots], xch_bar[kSkSlots], scl_bar[kSkSlots];
     __shared__ __align__(8) float xch[kSkSlots][kSkCluster];  // the cluster's row sums, slot = row mod 8
     __shared__ float red[kSkSlots][NW];                        // the compute warps' sums, slot = row mod 8
+    __shared__ float scl[kSkSlots];                            // 1 / (the row's sum), slot = row mod 8
     __shared__ float f_stage[kSkMaxRows];                      // f' of this cluster's rows
     __shared__ int abort_flag;
 
@@ -419,6 +421,7 @@ __global__ void __cluster_dims__(kSkCluster, 1, 1) __launch_bounds__(kSkFusedThr
             // a row's exchange completes with this CTA's own sum (one arrival, which also
             // expects the other CTAs' bytes) and the 3 x 4 bytes they store asynchronously
             mbar_init(smem_u32(&xch_bar[b]), 1);
+            mbar_init(smem_u32(&scl_bar[b]), 1);
         }
         abort_flag = 0;
         fence_mbar_init();
@@ -440,11 +443,26 @@ __global__ void __cluster_dims__(kSkCluster, 1, 1) __launch_bounds__(kSkFusedThr
 
     int issued = K < kSkBuffers ? K : kSkBuffers;
     if (warp == NW) {
-        // ---------------- control warp: the CTA's row sums, the exchange, the copies
+        // ---------------- control warp: the CTA's row sums, the exchange, the copies,
+        // and the row scalings
         if (lane == 0) {
+            // row tp's cluster sum S (the four CTAs' sums in rank order: the same bits in
+            // every CTA), 1 / S for the compute warps, and f_tp = f'_tp - log2(S) / c
+            auto scale_row = [&](int tp) -> bool {
+                const int slot = tp % kSkSlots;
+                if (!wait(xbar_base + 8u * (uint32_t)slot, (uint32_t)(tp / kSkSlots) & 1u)) return false;
+                float S = xch[slot][0];
+                for (int r = 1; r < kSkCluster; ++r) S += xch[slot][r];
+                if (rank == 0) f[cid + tp * ncl] = f_stage[tp] - __log2f(S) / c;
+                scl[slot] = 1.0f / S;
+                mbar_arrive(smem_u32(&scl_bar[slot]));
+                return true;
+            };
             for (int t = 0; t < issued; ++t) issue(t);
             for (int t = 0; t < K; ++t) {
                 const int slot = t % kSkSlots;
+                // the previous row's exchange has had a row of work to land
+                if (t >= 1 && !scale_row(t - 1)) break;
                 if (!wait(smem_u32(&sums_bar[slot]), (uint32_t)(t / kSkSlots) & 1u)) break;
                 float cs = 0.0f;
                 for (int w = 0; w < NW; ++w) cs += red[slot][w];  // warp order: fixed
@@ -458,6 +476,7 @@ __global__ void __cluster_dims__(kSkCluster, 1, 1) __launch_bounds__(kSkFusedThr
                 // every compute warp has read row t (its exponents are in registers):
                 // its buffer takes row t + kSkBuffers
                 if (issued < K) issue(issued++);
+                if (t == K - 1) scale_row(t);
             }
         }
     } else {
@@ -490,16 +509,11 @@ __global__ void __cluster_dims__(kSkCluster, 1, 1) __launch_bounds__(kSkFusedThr
             }
             return true;
         };
-        // row tp's cluster sum S, f_tp, and its entries e / S into the column sums
+        // row tp's entries e / S into the column sums
         auto row_acc = [&](int tp, const float (&e)[CPT]) -> bool {
             const int slot = tp % kSkSlots;
-            if (!wait(xbar_base + 8u * (uint32_t)slot, (uint32_t)(tp / kSkSlots) & 1u)) return false;
-            // rank order: the same bits in every CTA of the cluster
-            float S = xch[slot][0];
-#pragma unroll
-            for (int r = 1; r < kSkCluster; ++r) S += xch[slot][r];
-            if (rank == 0 && tid == 0) f[cid + tp * ncl] = f_stage[tp] - __log2f(S) / c;
-            const float scale = 1.0f / S;
+            if (!wait(smem_u32(&scl_bar[slot]), (uint32_t)(tp / kSkSlots) & 1u)) return false;
+            const float scale = scl[slot];
 #pragma unroll
             for (int q = 0; q < CPT; ++q) acc[q] = fmaf(e[q], scale, acc[q]);
             if ((tp & 15) == 15) {
@@ -698,7 +712,7 @@ static bool sinkhorn_fused(const float *G, int n, float *f, float *g, double *pa
                            cudaStream_t s) {
     const int W = n / kSkCluster;
     const size_t smem = ((size_t)kSkBuffers * W + (size_t)16 * kSkFusedThreads) * sizeof(float);
-    // n >= kSkFusedMinN: W > 4096 columns, at most 16 a thread.  The kernel is
+    // n >= kSkFusedMinN: W >= 5120 columns, at most 16 a thread.  The kernel is
     // configured once for the largest quarter-row it takes (W = 512 * 16); the
     // clusters that fit in one wave are found once per n.
     auto kern = k_sk_fused<16>;
