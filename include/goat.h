@@ -298,6 +298,11 @@ typedef struct goat_lap_options {
                              and end the sequential bidding, default max(128, n / 256)        */
     long long sap_pops;   /* row scans the shortest-augmenting-path searches may do per phase,
                              default 8n + 2^16 (64n + 2^20 in the last phase); 0 disables them */
+    int head_stall;       /* Jacobi rounds in a row without fewer bidders than before that end
+                             a phase's rounds, default 16                                    */
+    int sap_every_phase;  /* 1: the searches complete every eps phase; 0 (default): only the
+                             last, earlier phases leave their stalled rows unassigned (their
+                             prices still start the next phase)                             */
 } goat_lap_options;
 
 /* What one projection did. */

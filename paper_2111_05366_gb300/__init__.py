@@ -77,7 +77,8 @@ class goat_stats(ctypes.Structure):
 
 class goat_lap_options(ctypes.Structure):
     _fields_ = [("max_rounds", ctypes.c_int), ("head_rounds", ctypes.c_int), ("tail_bids", ctypes.c_longlong),
-                ("tail_stall", ctypes.c_longlong), ("sap_pops", ctypes.c_longlong)]
+                ("tail_stall", ctypes.c_longlong), ("sap_pops", ctypes.c_longlong), ("head_stall", ctypes.c_int),
+                ("sap_every_phase", ctypes.c_int)]
 
 
 class goat_lap_info(ctypes.Structure):

@@ -955,6 +955,8 @@ void goat_lap_default_options(goat_lap_options *o) {
     o->tail_bids = c.tail_bids;
     o->tail_stall = c.tail_stall;
     o->sap_pops = c.sap_pops;
+    o->head_stall = c.head_stall;
+    o->sap_every_phase = c.sap_every_phase;
 }
 
 int goat_project_ex(const float *M, int n, int maximize, const goat_lap_options *opts, int32_t *perm_out,
@@ -973,6 +975,8 @@ int goat_project_ex(const float *M, int n, int maximize, const goat_lap_options 
         ctl.tail_bids = opts->tail_bids;
         ctl.tail_stall = opts->tail_stall;
         ctl.sap_pops = opts->sap_pops;
+        if (opts->head_stall > 0) ctl.head_stall = opts->head_stall;
+        if (opts->sap_every_phase >= 0) ctl.sap_every_phase = opts->sap_every_phase;
     }
     const Plan w = make_plan(Shape{n, 0, 0}, GOAT_DTYPE_U8, GOAT_PREC_BF16, NEED_LAP);
     Scratch ws;

@@ -41,6 +41,7 @@ struct DevState {
     int lap_unassigned;   // auction: bidders without an object
     int lap_free;         // shortest-augmenting-path step: rows it has to place
     int lap_nb[2];        // Jacobi bidder list lengths (alternate rounds)
+    int lap_head[2];      // rounds run by the last persistent Jacobi head, and its final list
     int asym_count;
     int bad_perm;
     long long lap_bids;   // Gauss-Seidel bids of the projection so far

@@ -18,26 +18,30 @@
 // of the quantised matrix is a multiple of Qm, so it is optimal for that matrix:
 // an exact LAP, no tolerance involved.
 //
-// Scheduling.  Parallel Jacobi rounds while many rows bid; the long tail of a
-// phase (a few rows evicting each other) runs in Gauss-Seidel order in one CTA,
-// or for n >= 4096 in a cluster of 8 CTAs that split the columns.  When that tail
-// stops shrinking (a few rows chasing the last free objects through a large set
-// of near-tied objects: each bid lifts one price by about eps, so closing a gap
-// of D costs about |set| D / eps bids), the remaining rows are placed by
-// shortest augmenting paths instead (Jonker-Volgenant's Dijkstra step, one
-// search per row, exact integer duals).  The search runs on the matrix a~ that
+// Scheduling.  Each phase starts with parallel Jacobi rounds (one cooperative
+// launch per phase) while many rows bid, until at most 4 rows bid or the number of
+// bidders has not fallen for 16 rounds; the long tail of a phase (a few rows
+// evicting each other) then runs in Gauss-Seidel order in one CTA, or for
+// n >= 4096 in a cluster of 8 CTAs that split the columns.  Rows that still chase
+// the last free objects through a large set of near-tied objects (each bid lifts
+// one price by about eps, so closing a gap of D costs about |set| D / eps bids)
+// are left to the next phase, which starts from the prices alone; in the last
+// phase they are placed by shortest augmenting paths instead (Jonker-Volgenant's
+// Dijkstra step, exact integer duals).  The search runs on the matrix a~ that
 // adds to each assigned pair its eps-complementary-slackness slack
 // delta_i = max_j (a_ij - p_j) - (a_i,j_i - p_j_i) in [0, eps], so that the
 // auction's prices and assignment are an exactly feasible, tight starting point.
 // Every assignment value of a~ is within n eps of that of a; in the last phase
-// (eps = 1 < Qm / n) an optimum of a~ is therefore an optimum of a.  A phase thus
-// always ends complete, and its prices are a sound start for the next one.
+// (eps = 1 < Qm / n) an optimum of a~ is therefore an optimum of a, so the last
+// phase ends complete and optimal.  (The searches can also complete every phase:
+// goat_lap_options.sap_every_phase.)
 // Budgets bound the time on degenerate inputs: if the last phase still runs out,
 // the free rows are filled greedily and the returned duality gap says how far
 // from optimal that is (0 when the proof above applies).
 #include <algorithm>
 #include <chrono>
 #include <climits>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 
@@ -229,19 +233,17 @@ __device__ __forceinline__ void list_append(bool want, int row, int *dst, int *c
     if (want) dst[base + __popc(m & ((1u << lane) - 1u))] = row;
 }
 
-// Jacobi bidding over the rows listed for this round (blist[cur], lap_nb[cur]
-// entries): one CTA per bidding row (a row of 4n bytes is too long for one warp
-// to stream at speed); the next round's list starts empty.
+// Jacobi bidding over the rows listed for this round (blist[cur], cnt entries):
+// one CTA per bidding row (a row of 4n bytes is too long for one warp to stream at
+// speed), CTAs blk, blk + nblk, ...
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_lap_bid(const float *__restrict__ M, int n, const Quant q,
-                                                     const LapBuffers L, i64 eps, DevState *st, int cur) {
-    const int cnt = st->lap_nb[cur];
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->lap_nb[cur ^ 1] = 0;
+__device__ __forceinline__ void bid_rows(const float *__restrict__ M, int n, const Quant q, const LapBuffers &L,
+                                         i64 eps, int cur, int cnt, int blk, int nblk) {
     constexpr int NW = THREADS / 32;
     __shared__ i64 s_b1[NW], s_b2[NW];
     __shared__ int s_j1[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
+    for (int idx = blk; idx < cnt; idx += nblk) {
         const int i = L.blist[cur][idx];
         i64 b1 = kNegInf, b2 = kNegInf;
         int j1 = INT_MAX;
@@ -266,10 +268,10 @@ __global__ void __launch_bounds__(THREADS) k_lap_bid(const float *__restrict__ M
     }
 }
 
-// Each object's winner: the highest bid, the lowest row among equal ones.
-__global__ void k_lap_win(const LapBuffers L, const DevState *st, int cur) {
-    const int cnt = st->lap_nb[cur];
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+// Each object's winner: the highest bid, the lowest row among equal ones
+// (threads t, t + nthr, ... of the bidders).
+__device__ __forceinline__ void win_rows(const LapBuffers &L, int cur, int cnt, int t, int nthr) {
+    for (int k = t; k < cnt; k += nthr) {
         const int i = L.blist[cur][k];
         const int j = L.my_obj[i];
         if (L.bbest[j] == (unsigned long long)L.my_bid[i]) atomicMin(&L.bwin[j], i);
@@ -279,15 +281,14 @@ __global__ void k_lap_win(const LapBuffers L, const DevState *st, int cur) {
 // Winners take their objects at their bids and evict the previous holders; the
 // evicted rows and the outbid bidders make up the next round's list.  (An outbid
 // row reads bwin[j] while the winner may be resetting it: either value differs
-// from the outbid row, so the outcome is the same.)
-__global__ void k_lap_assign(const LapBuffers L, DevState *st, int cur) {
-    const int cnt = st->lap_nb[cur];
+// from the outbid row, so the outcome is the same.)  `t` and `nthr` cover whole
+// warps (the list appends take warp ballots).
+__device__ __forceinline__ void assign_rows(const LapBuffers &L, DevState *st, int cur, int cnt, int t, int nthr) {
     int *next = L.blist[cur ^ 1];
     int *ncount = &st->lap_nb[cur ^ 1];
-    const int stride = gridDim.x * blockDim.x;
-    const int rounds = (cnt + stride - 1) / stride;  // uniform trip count for the warp ballots
+    const int rounds = (cnt + nthr - 1) / nthr;  // uniform trip count for the warp ballots
     for (int r = 0; r < rounds; ++r) {
-        const int k = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        const int k = r * nthr + t;
         int push = -1;
         if (k < cnt) {
             const int i = L.blist[cur][k];
@@ -308,6 +309,66 @@ __global__ void k_lap_assign(const LapBuffers L, DevState *st, int cur) {
             }
         }
         list_append(push >= 0, push, next, ncount);
+    }
+}
+
+// One Jacobi round as three launches (the form used without cooperative launch).
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_lap_bid(const float *__restrict__ M, int n, const Quant q,
+                                                     const LapBuffers L, i64 eps, DevState *st, int cur) {
+    const int cnt = st->lap_nb[cur];
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->lap_nb[cur ^ 1] = 0;  // the next round's list starts empty
+    bid_rows<THREADS>(M, n, q, L, eps, cur, cnt, blockIdx.x, gridDim.x);
+}
+
+__global__ void k_lap_win(const LapBuffers L, const DevState *st, int cur) {
+    win_rows(L, cur, st->lap_nb[cur], blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+__global__ void k_lap_assign(const LapBuffers L, DevState *st, int cur) {
+    assign_rows(L, st, cur, st->lap_nb[cur], blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// The Jacobi rounds of one eps phase in one cooperative launch: a round's bids,
+// winners and assignments are separated by grid barriers, and the rounds go on
+// while more than `threshold` rows bid, at most max_rounds of them, and until
+// `stall` rounds in a row have not brought the number of bidders below its least
+// value so far (rows chasing each other through near-tied objects, which the
+// later steps place far sooner).  The list lengths are read after a barrier, so
+// every block takes the same path.  Writes the rounds run and the index of the
+// list left to bid into st->lap_head.
+constexpr int LAP_HEAD_THREADS = 1024;
+static_assert(offsetof(DevState, lap_head) == offsetof(DevState, lap_nb) + 2 * sizeof(int),
+              "the head's report is read with the list lengths in one copy");
+__global__ void __launch_bounds__(LAP_HEAD_THREADS, 1)
+    k_lap_head(const float *__restrict__ M, int n, const Quant q, const LapBuffers L, i64 eps, DevState *st,
+               int cur, int max_rounds, int threshold, int stall) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    volatile int *nb = st->lap_nb;
+    int r = 0, least = INT_MAX, since = 0;
+    for (; r < max_rounds; ++r) {
+        const int cnt = nb[cur];
+        if (cnt <= threshold) break;
+        if (cnt < least) {
+            least = cnt;
+            since = 0;
+        } else if (++since >= stall) {
+            break;
+        }
+        if (t == 0) nb[cur ^ 1] = 0;  // read by the assignments, two barriers on
+        bid_rows<LAP_HEAD_THREADS>(M, n, q, L, eps, cur, cnt, blockIdx.x, gridDim.x);
+        grid.sync();
+        win_rows(L, cur, cnt, t, nthr);
+        grid.sync();
+        assign_rows(L, st, cur, cnt, t, nthr);
+        grid.sync();
+        cur ^= 1;
+    }
+    if (t == 0) {
+        st->lap_head[0] = r;
+        st->lap_head[1] = cur;
     }
 }
 
@@ -1181,6 +1242,8 @@ void lap_default_control(LapControl *c) {
     c->tail_stall = -1;
     c->sap_pops = -1;
     c->sap_step = -1;
+    c->head_stall = 16;
+    c->sap_every_phase = 0;
 }
 
 // Runs the projection.  lap_ws must hold lap_bytes(n, ...) bytes; cost_dev
@@ -1227,6 +1290,7 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
     int rounds = 0;
     bool exhausted = false;
     const int head_threshold = 4;
+    const int head_stall = ctl.head_stall > 0 ? ctl.head_stall : INT_MAX;
     // the cluster kernels hold per-column state of n / 8 columns in each CTA's shared memory
     const int cw = (n + LAP_CLUSTER - 1) / LAP_CLUSTER;
     const size_t tail_smem = (size_t)cw * (sizeof(i64) + sizeof(int));
@@ -1252,6 +1316,17 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
         if (sap_cpt) sap_grid = (int)std::max<int64_t>(1, ceil_div(n, (int64_t)SAP_SLOTS * sap_cpt));
     }
     const bool use_sap = sap_cpt > 0;
+    // the Jacobi rounds: one cooperative launch per phase (one CTA per SM), else
+    // three launches per round
+    int head_grid = 0;
+    {
+        int coop = 0, occ = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lap_head, LAP_HEAD_THREADS, 0) == cudaSuccess &&
+            occ >= 1)
+            head_grid = sms * std::min(occ, 1);
+        cudaGetLastError();
+    }
     const long long stall = ctl.tail_stall >= 0 ? ctl.tail_stall : std::max(128LL, (long long)n / 256);
     for (;;) {
         const bool last = eps <= 1;
@@ -1261,7 +1336,29 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
         int left = n;
         auto t0 = clk::now();
         int cur = 0;  // the list the next round bids from
-        for (int hr = 0; hr < ctl.head_rounds && rounds < ctl.max_rounds; hr += 4) {
+        if (head_grid > 0 && ctl.head_rounds > 0 && rounds < ctl.max_rounds) {
+            // all of the phase's rounds in one launch, one poll
+            const float *Mp = M;
+            int nn = n, c0 = 0, maxr = std::min(ctl.head_rounds, ctl.max_rounds - rounds), thr = head_threshold,
+                hstall = head_stall;
+            Quant qq = q;
+            LapBuffers LL = L;
+            i64 ee = eps;
+            DevState *stp = st;
+            void *args[] = {(void *)&Mp, (void *)&nn, (void *)&qq, (void *)&LL, (void *)&ee, (void *)&stp,
+                            (void *)&c0, (void *)&maxr, (void *)&thr, (void *)&hstall};
+            if (cudaLaunchCooperativeKernel((const void *)k_lap_head, dim3(head_grid), dim3(LAP_HEAD_THREADS), args, 0,
+                                            s) != cudaSuccess)
+                return GOAT_ERR_CUDA;
+            note_launches(1);
+            // lap_nb[0..1] and lap_head[0..1] are adjacent (host_pinned holds 64 ints)
+            cudaMemcpyAsync(host_pinned, st->lap_nb, 4 * sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (cudaStreamSynchronize(s) != cudaSuccess) return GOAT_ERR_CUDA;
+            rounds += host_pinned[2];
+            cur = host_pinned[3] & 1;
+            left = host_pinned[cur];
+        }
+        for (int hr = 0; head_grid == 0 && hr < ctl.head_rounds && rounds < ctl.max_rounds; hr += 4) {
             // many bidders: many CTAs of 256 threads; few: one 1024-thread CTA per row
             const bool light = left <= sms;
             const int gb = light ? std::max(1, left) : growb;
@@ -1296,7 +1393,9 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
             left = poll_int(&st->lap_unassigned, host_pinned, s);
             R.ms_tail += ms_since(t0);
         }
-        if (left > 0 && use_sap) {
+        // the searches complete the last phase; earlier phases only refine the prices,
+        // and rows they leave unassigned start the next phase like every other row
+        if (left > 0 && use_sap && (last || ctl.sap_every_phase)) {
             t0 = clk::now();
             const long long pops =
                 ctl.sap_pops > 0 ? ctl.sap_pops : (last ? 64LL * n + (1LL << 20) : 8LL * n + (1LL << 16));

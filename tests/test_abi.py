@@ -85,6 +85,7 @@ def test_projection_schedule_defaults(lib_path):
     o = goat.lap_options()
     assert o.max_rounds == 1 << 20 and o.head_rounds == 256
     assert o.tail_bids == -1 and o.tail_stall == -1 and o.sap_pops == -1
+    assert o.head_stall == 16 and o.sap_every_phase == 0
     o = goat.lap_options(tail_bids=0, sap_pops=7)
     assert o.tail_bids == 0 and o.sap_pops == 7
 
