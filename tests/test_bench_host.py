@@ -52,3 +52,18 @@ def test_traffic_is_dropped_when_the_kernel_source_changes(tmp_path):
     assert bench.gemm_traffic_per_launch(1000, "t.txt") is None
     assert bench.gemm_traffic_per_launch(1000, "missing.txt") is None
     shutil.rmtree(root)
+
+
+def test_cpu_baseline_sample_runs_the_oracle_on_every_core_with_one_sinkhorn_count():
+    # the cpu_baseline leg and the reference arm time the same oracle calls on all host
+    # cores (a disjoint row block per thread) and charge the same Sinkhorn iterations
+    # per FW iteration; here on a small pair so that the CPU suite stays fast
+    bench = _bench()
+    from paper_2111_05366_gb300 import synthetic
+    gp = synthetic.large_sbm_pair(512, seed=5)
+    r = bench.cpu_oracle_sample(gp, 2, cores=3)
+    assert r["kind"] == "oracle" and r["cores"] == 3 and r["unit"] == bench.UNIT
+    assert r["sinkhorn_iters_per_fw_iter"] == bench.SK_ITERS_PER_FW
+    assert r["value"] > 0 and r["value"] == pytest.approx(1.0 / r["seconds_per_fw_iter"])
+    assert "6 rows" in r["sample"] and "3 threads" in r["sample"]
+    assert bench.host_cores() >= 1
