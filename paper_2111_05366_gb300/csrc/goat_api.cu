@@ -103,7 +103,8 @@ static Plan make_plan(const Shape &sh, int dtype, int precision, int need) {
         w.G = take(nn * 4);
         w.f = take((size_t)n * 4);
         w.g = take((size_t)n * 4);
-        w.mlp = take(mlp_warm_start_scratch_bytes(n));
+        // the network's features (only plain solves take network weights)
+        if (sh.m == 0 && !sh.dir) w.mlp = take(mlp_warm_start_scratch_bytes(n));
         w.rearr = take(rearrangement_scratch_bytes(n));
     }
     if (need & (NEED_SK | NEED_FW)) {

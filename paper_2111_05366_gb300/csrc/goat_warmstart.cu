@@ -76,43 +76,77 @@ __global__ void __launch_bounds__(256) k_feat_rows(const float *__restrict__ G, 
     }
 }
 
-// Column statistics of G: a CTA takes 32 columns (one 128-byte segment per row)
-// and 8 row groups; each thread runs over rows g, g + 8, ... and the groups are
-// merged in shared memory in a fixed order.
-__global__ void __launch_bounds__(256) k_feat_cols(const float *__restrict__ G, int n, float inv_eps,
-                                                   float *__restrict__ stats) {
-    __shared__ float sh[4][8][33];
-    const int c = threadIdx.x & 31, rg = threadIdx.x >> 5;
-    const int j = blockIdx.x * 32 + c;
+// Column statistics of G in two steps.  k_feat_colpart: a CTA takes 1024 columns
+// (4 adjacent ones per thread: float4 loads when G is 16-byte aligned and n a
+// multiple of 4, else scalar) and one chunk of rows, four rows' loads in flight;
+// it writes the chunk's sum, sum of squares, max and min of every column (in units
+// of eps).  k_feat_colmerge adds the chunks in chunk order, so the result does not
+// depend on the launch's timing.
+constexpr int kFeatColsPerCta = 1024;
+constexpr int kFeatMaxChunks = 64;
+
+__global__ void __launch_bounds__(256) k_feat_colpart(const float *__restrict__ G, int n, float inv_eps,
+                                                      int rows_per_chunk, float4 *__restrict__ part) {
+    const int j0 = blockIdx.x * kFeatColsPerCta + 4 * threadIdx.x;
+    if (j0 >= n) return;
+    const int r0 = blockIdx.y * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+    const bool vec = (j0 + 3 < n) && (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(G) & 15) == 0);
+    const int kmax = min(4, n - j0);
+    float s[4], s2[4], mx[4], mn[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        s[k] = 0.f;
+        s2[k] = 0.f;
+        mx[k] = -INFINITY;
+        mn[k] = INFINITY;
+    }
+    auto add = [&](int k, float x) {
+        const float v = x * inv_eps;
+        s[k] += v;
+        s2[k] = fmaf(v, v, s2[k]);
+        mx[k] = fmaxf(mx[k], v);
+        mn[k] = fminf(mn[k], v);
+    };
+    int i = r0;
+    if (vec) {
+        for (; i + 3 < r1; i += 4) {
+            float4 a[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = __ldg(reinterpret_cast<const float4 *>(G + (long long)(i + u) * n + j0));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                add(0, a[u].x);
+                add(1, a[u].y);
+                add(2, a[u].z);
+                add(3, a[u].w);
+            }
+        }
+    }
+    for (; i < r1; ++i) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < kmax) add(k, __ldg(G + (long long)i * n + j0 + k));
+    }
+    for (int k = 0; k < kmax; ++k) part[(size_t)blockIdx.y * n + j0 + k] = make_float4(s[k], s2[k], mx[k], mn[k]);
+}
+
+__global__ void k_feat_colmerge(const float4 *__restrict__ part, int chunks, int n, float *__restrict__ stats) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
     float s = 0.f, s2 = 0.f, mx = -INFINITY, mn = INFINITY;
-    if (j < n) {
-        for (int i = rg; i < n; i += 8) {
-            const float x = G[(long long)i * n + j] * inv_eps;
-            s += x;
-            s2 += x * x;
-            mx = fmaxf(mx, x);
-            mn = fminf(mn, x);
-        }
+    for (int c = 0; c < chunks; ++c) {
+        const float4 p = part[(size_t)c * n + j];
+        s += p.x;
+        s2 += p.y;
+        mx = fmaxf(mx, p.z);
+        mn = fminf(mn, p.w);
     }
-    sh[0][rg][c] = s;
-    sh[1][rg][c] = s2;
-    sh[2][rg][c] = mx;
-    sh[3][rg][c] = mn;
-    __syncthreads();
-    if (rg == 0 && j < n) {
-        for (int g = 1; g < 8; ++g) {
-            s += sh[0][g][c];
-            s2 += sh[1][g][c];
-            mx = fmaxf(mx, sh[2][g][c]);
-            mn = fminf(mn, sh[3][g][c]);
-        }
-        const float mean = s / n;
-        float *o = stats + (long long)(n + j) * 4;
-        o[0] = mean;
-        o[1] = mx;
-        o[2] = sqrtf(fmaxf(s2 / n - mean * mean, 0.f));
-        o[3] = mn;
-    }
+    const float mean = s / n;
+    float *o = stats + (long long)(n + j) * 4;
+    o[0] = mean;
+    o[1] = mx;
+    o[2] = sqrtf(fmaxf(s2 / n - mean * mean, 0.f));
+    o[3] = mn;
 }
 
 // 2-hop degrees (A d_A)_i and (B d_B)_j (one warp per row).
@@ -271,11 +305,25 @@ __global__ void k_mlp_adam(float *__restrict__ master, float *__restrict__ m, fl
 
 // ---------------------------------------------------------------- host wrappers
 
+// Row chunks of the column statistics: as many as fill one wave of 8 CTAs per SM,
+// at least 32 rows each, at most kFeatMaxChunks.
+static int feat_col_chunks(int n) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long tiles = ceil_div(n, kFeatColsPerCta);
+    long long c = std::max<long long>(1, (long long)sms * 8 / tiles);
+    c = std::min<long long>(c, std::max<long long>(1, n / 32));
+    return (int)std::min<long long>(c, kFeatMaxChunks);
+}
+
 int dual_features(const float *G, const void *A, const void *B, int n, int dtype, float eps, float *feats,
                   float *scratch, cudaStream_t s) {
-    // scratch: stats 8n floats, deg 2n, hop2 2n, sums 4 doubles (16-byte aligned after 12n floats)
+    // scratch: stats 8n floats, deg 2n, hop2 2n, sums 4 doubles, then (16-byte aligned)
+    // the column chunks' partial statistics, kFeatMaxChunks x n float4
     float *stats = scratch, *deg = scratch + 8LL * n, *hop2 = deg + 2LL * n;
     double *sums = reinterpret_cast<double *>(hop2 + round_up(2LL * n, 4));
+    float4 *colpart = reinterpret_cast<float4 *>(round_up(reinterpret_cast<uintptr_t>(sums + 4), 16));
     cudaMemsetAsync(sums, 0, 4 * sizeof(double), s);
     const int gw = (int)std::max<long long>(1, std::min<long long>(ceil_div(n, 8), 152LL * 16));
     const float inv_eps = 1.0f / eps;
@@ -287,13 +335,18 @@ int dual_features(const float *G, const void *A, const void *B, int n, int dtype
         k_feat_rows<float><<<gw, 256, 0, s>>>(G, (const float *)A, (const float *)B, n, inv_eps, stats, deg, sums);
         k_feat_hop2<float><<<gw, 256, 0, s>>>((const float *)A, (const float *)B, n, deg, hop2, sums);
     }
-    k_feat_cols<<<(unsigned)ceil_div(n, 32), 256, 0, s>>>(G, n, inv_eps, stats);
+    const int chunks = feat_col_chunks(n);
+    k_feat_colpart<<<dim3((unsigned)ceil_div(n, kFeatColsPerCta), chunks), 256, 0, s>>>(
+        G, n, inv_eps, (int)ceil_div(n, chunks), colpart);
+    k_feat_colmerge<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(colpart, chunks, n, stats);
     k_feat_assemble<<<(unsigned)ceil_div(2LL * n, 256), 256, 0, s>>>(n, stats, deg, hop2, sums, feats);
-    note_launches(4);
+    note_launches(5);
     return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
 }
 
-size_t dual_features_scratch_bytes(int n) { return (size_t)(12LL * n + 8) * sizeof(float) + 4 * sizeof(double); }
+size_t dual_features_scratch_bytes(int n) {
+    return (size_t)(12LL * n + 8) * sizeof(float) + 4 * sizeof(double) + 16 + (size_t)kFeatMaxChunks * n * sizeof(float4);
+}
 
 int mlp_forward(const __nv_bfloat16 *w, const float *x, int N, float *y, cudaStream_t s) {
     const int grid = (int)std::max<long long>(1, std::min<long long>(ceil_div(N, 256), 152LL * 8));

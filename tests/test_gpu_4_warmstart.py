@@ -23,9 +23,10 @@ def _bf16_params(seed):
     return wb, wb.float().cpu().double().numpy()  # the exact BF16 values, for the oracle
 
 
-@pytest.mark.parametrize("weighted", [False, True])
-def test_features_match_oracle(weighted):
-    n = 211
+# n = 211: scalar column loads, a ragged last group of columns; n = 1028: float4 loads,
+# two 1024-column tiles (the second holds one group), several row chunks
+@pytest.mark.parametrize("n,weighted", [(211, False), (211, True), (1028, True)])
+def test_features_match_oracle(n, weighted):
     gp = synthetic.rho_er_pair(n, 0.1, 0.8, seed=9, weighted=weighted)
     A, B = torch.from_numpy(gp.A).cuda(), torch.from_numpy(gp.B).cuda()
     rng = np.random.default_rng(1)

@@ -112,9 +112,16 @@ def test_seeded_directed_follows_oracle():
 
 
 def test_seeded_workspace_and_bad_seed_counts():
-    n = 64
-    assert goat.workspace_bytes(n, seeds=10) > goat.workspace_bytes(n)
+    n, m = 64, 10
+    # the plan is laid out for the unseeded block: at least its FP32 G, P and the step's
+    # gradient, plus the seeds' constant term; a seeded solve runs in exactly that room
+    wb = goat.workspace_bytes(n, seeds=m)
+    assert wb >= 4 * 4 * (n - m) ** 2
     assert goat.workspace_bytes(n, seeds=n + 1) == 0
     gp = synthetic.rho_er_pair(n, 0.2, 0.9, seed=2)
+    ws = torch.empty(wb, dtype=torch.uint8, device="cuda")
+    perm, obj, _ = goat.goat_match(cuda(gp.A), cuda(gp.B), params=goat.default_params(seeds=m), workspace=ws)
+    np.testing.assert_array_equal(perm[:m], np.arange(m))
+    assert obj == oracle.objective_perm(gp.A, gp.B, perm)
     with pytest.raises(goat.GoatError):
         goat.goat_match(cuda(gp.A), cuda(gp.B), params=goat.default_params(seeds=n + 1))
