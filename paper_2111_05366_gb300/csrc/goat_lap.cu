@@ -268,6 +268,29 @@ __device__ __forceinline__ void bid_rows(const float *__restrict__ M, int n, con
     }
 }
 
+// The same bids with one warp per row (warps w, w + nwarps, ... of the grid): used
+// while at least as many rows bid as the grid has warps, where the CTA-wide
+// reductions and the bidding thread's serial step would stall a whole CTA per row.
+__device__ __forceinline__ void bid_rows_warp(const float *__restrict__ M, int n, const Quant q, const LapBuffers &L,
+                                              i64 eps, int cur, int cnt, int w, int nwarps) {
+    const int lane = threadIdx.x & 31;
+    for (int idx = w; idx < cnt; idx += nwarps) {
+        const int i = L.blist[cur][idx];
+        i64 b1 = kNegInf, b2 = kNegInf;
+        int j1 = INT_MAX;
+        top2_scan(M + (long long)i * n, L.price, n, q, lane, 32, i, b1, b2, j1);
+        top2_warp(b1, b2, j1);
+        if (lane == 0) {
+            j1 = tie_key_to_col(j1, i, n);
+            const i64 inc = (b2 == kNegInf) ? eps : (b1 - b2) + eps;
+            const i64 bid = L.price[j1] + inc;
+            L.my_obj[i] = j1;
+            L.my_bid[i] = bid;
+            atomicMax(&L.bbest[j1], (unsigned long long)bid);
+        }
+    }
+}
+
 // Each object's winner: the highest bid, the lowest row among equal ones
 // (threads t, t + nthr, ... of the bidders).
 __device__ __forceinline__ void win_rows(const LapBuffers &L, int cur, int cnt, int t, int nthr) {
@@ -358,7 +381,10 @@ __global__ void __launch_bounds__(LAP_HEAD_THREADS, 1)
             break;
         }
         if (t == 0) nb[cur ^ 1] = 0;  // read by the assignments, two barriers on
-        bid_rows<LAP_HEAD_THREADS>(M, n, q, L, eps, cur, cnt, blockIdx.x, gridDim.x);
+        if (cnt >= nthr / 32)
+            bid_rows_warp(M, n, q, L, eps, cur, cnt, t >> 5, nthr >> 5);
+        else
+            bid_rows<LAP_HEAD_THREADS>(M, n, q, L, eps, cur, cnt, blockIdx.x, gridDim.x);
         grid.sync();
         win_rows(L, cur, cnt, t, nthr);
         grid.sync();
