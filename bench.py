@@ -207,7 +207,8 @@ def gemm_roofline(precision: str, n: int, ms_per_launch: float, peaks: dict, nnz
                   "bf16split": "k_gemm_xyT (BF16 kind::f16; product 2 over the two terms of Q B, K = 2n)",
                   "fp32": "k_gemm_xyT (BF16 kind::f16 over two split terms, K = 2n, in K chunks)"}[precision]
         peak_source = f"{peaks['source']} bf16_tflops_sustained"
-        traffic = gemm_traffic_per_launch(n) if precision == "bf16" else None
+        traffic = {"bf16": gemm_traffic_per_launch(n),
+                   "bf16split": gemm_traffic_per_launch(n, "k_gemm_xyT_split_traffic.txt")}.get(precision)
     sec = ms_per_launch / 1000.0
     achieved = executed / sec / 1e12
     # A and B are ~1 % dense: of the dense FLOP only 2 nnz(B) n (C1 = B Q^T) and
