@@ -7,9 +7,11 @@ barycenter init, up to 30 Frank-Wolfe iterations, final GPU linear assignment.
 A "step" is one whole solve (goat_match: gradient products, Sinkhorn, line
 search, update for every FW iteration, then the projection and the exact
 objective).  The metric is FW iterations per second of the chosen form
-(BF16 tensor-core products, FP32 log-domain Sinkhorn warm-started from the
-previous step's duals), reported next to the plain FP32-accurate GPU form
-(two-term BF16 split products, cold-started Sinkhorn) at the same workload.
+(tensor-core products with Q in BF16 and the intermediate Q B as a BF16 hi term
+plus an E4M3 lo term -- the form whose matching accuracy equals the FP64
+oracle's -- and FP32 log-domain Sinkhorn warm-started from the previous step's
+duals), reported next to the other forms and the plain FP32-accurate GPU form
+(two-term BF16 split products, cold- and warm-started Sinkhorn) on the same pair.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -55,7 +57,7 @@ def parse():
     ap.add_argument("--sk-max-iter", type=int, default=500)
     ap.add_argument("--seed", type=int, default=3000)
     ap.add_argument("--plain-steps", type=int, default=1)
-    ap.add_argument("--chosen", choices=["bf16split", "fp8", "bf16"], default="bf16split",
+    ap.add_argument("--chosen", choices=["bf16split", "bf16split8", "fp8", "bf16"], default="bf16split8",
                     help="product form of the timed (chosen) solve; the other forms are reported beside it")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-rows-per-core", type=int, default=4,
@@ -75,7 +77,7 @@ def parse():
                     default=None,
                     help="run only one step kind a few times on the workload (the small cases profiled with ncu)")
     ap.add_argument("--repeat", type=int, default=3)
-    ap.add_argument("--precision", choices=["bf16", "fp8", "fp32", "bf16split"], default="bf16",
+    ap.add_argument("--precision", choices=["bf16", "fp8", "fp32", "bf16split", "bf16split8"], default="bf16",
                     help="form of the products in --kernel-case gemm")
     return ap.parse_args()
 
@@ -181,11 +183,13 @@ def gemm_traffic_per_launch(n: int, name: str = "k_gemm_xyT_traffic.txt"):
 
 # ------------------------------------------------------------------ per-form report
 
-FORM_PRECISION = {"fp8": 2, "bf16": 0, "fp32": 1, "bf16split": 3}
+FORM_PRECISION = {"fp8": 2, "bf16": 0, "fp32": 1, "bf16split": 3, "bf16split8": 5}
 # BF16 MMA passes of (product 1, product 2) relative to one n x n x n BF16 product:
 # the FP32 form splits Q and Q B in two terms (K = 2n in both products), the split
-# form only Q B (product 2); the 8-bit form runs its passes at twice the BF16 rate
-FORM_PASSES = {"fp8": (1.0, 1.0), "bf16": (1.0, 1.0), "fp32": (2.0, 2.0), "bf16split": (1.0, 2.0)}
+# form only Q B (product 2); the 8-bit form runs its passes at twice the BF16 rate,
+# the split8 form the lo pass of its second product (1.5 BF16-equivalent passes)
+FORM_PASSES = {"fp8": (1.0, 1.0), "bf16": (1.0, 1.0), "fp32": (2.0, 2.0), "bf16split": (1.0, 2.0),
+               "bf16split8": (1.0, 1.5)}
 
 
 def gemm_roofline(precision: str, n: int, ms_per_launch: float, peaks: dict, nnz: float):
@@ -205,10 +209,13 @@ def gemm_roofline(precision: str, n: int, ms_per_launch: float, peaks: dict, nnz
         peak = peaks["bf16_tflops_sustained"]
         kernel = {"bf16": "k_gemm_xyT (BF16 kind::f16, one n x n x n product per launch)",
                   "bf16split": "k_gemm_xyT (BF16 kind::f16; product 2 over the two terms of Q B, K = 2n)",
+                  "bf16split8": "k_gemm_xyT (BF16 kind::f16; product 2: the hi term of Q B in BF16, its lo "
+                                "term in E4M3 kind::f8f6f4, one accumulator)",
                   "fp32": "k_gemm_xyT (BF16 kind::f16 over two split terms, K = 2n, in K chunks)"}[precision]
         peak_source = f"{peaks['source']} bf16_tflops_sustained"
         traffic = {"bf16": gemm_traffic_per_launch(n),
-                   "bf16split": gemm_traffic_per_launch(n, "k_gemm_xyT_split_traffic.txt")}.get(precision)
+                   "bf16split": gemm_traffic_per_launch(n, "k_gemm_xyT_split_traffic.txt"),
+                   "bf16split8": gemm_traffic_per_launch(n, "k_gemm_xyT_split8_traffic.txt")}.get(precision)
     sec = ms_per_launch / 1000.0
     achieved = executed / sec / 1e12
     # A and B are ~1 % dense: of the dense FLOP only 2 nnz(B) n (C1 = B Q^T) and
@@ -698,7 +705,7 @@ def main():
                                  sk_max_iter=args.sk_max_iter, profile=1)
     others = {f"{k}_warm": goat.default_params(precision=FORM_PRECISION[k], sk_warm_start=1, sk_tol=args.sk_tol,
                                                sk_max_iter=args.sk_max_iter, profile=1)
-              for k in ("bf16split", "bf16", "fp8") if k != args.chosen}
+              for k in ("bf16split", "bf16split8", "bf16", "fp8") if k != args.chosen}
     plain = goat.default_params(precision=goat.GOAT_PREC_FP32, sk_warm_start=0, sk_tol=args.sk_tol,
                                 sk_max_iter=args.sk_max_iter, profile=1)
     plain_warm = goat.default_params(precision=goat.GOAT_PREC_FP32, sk_warm_start=1, sk_tol=args.sk_tol,
@@ -767,8 +774,10 @@ def main():
     fw_loop_value = sum_over_ranks(float(fw_iters)) / (max_over_ranks(ms_fw_loop) / 1000.0)
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-              "scaling": "weak", "vs_baseline": None, "dtype": "e4m3" if args.chosen == "fp8" else "bf16",
+              "scaling": "weak", "vs_baseline": None, "dtype": {"fp8": "e4m3", "bf16split8": "bf16+e4m3"}.get(args.chosen, "bf16"),
               "precision_form": {"bf16split": "BF16 products, Q B kept as two BF16 terms (GOAT_PREC_BF16_SPLIT)",
+                                 "bf16split8": "BF16 products, Q B as a BF16 hi term and an E4M3 lo term "
+                                               "(GOAT_PREC_BF16_SPLIT8)",
                                  "bf16": "BF16 products (GOAT_PREC_BF16)",
                                  "fp8": "E4M3 products (GOAT_PREC_FP8)"}[args.chosen],
               "data": "synthetic",
@@ -812,7 +821,7 @@ def main():
     if not args.no_accuracy and rank == 0:
         acc_forms = {f"{k}_{'warm' if w else 'cold'}": goat.default_params(
                          precision=FORM_PRECISION[k], sk_warm_start=w, sk_tol=args.sk_tol, sk_max_iter=args.sk_max_iter)
-                     for k in ("bf16split", "fp32", "bf16", "fp8") for w in (1, 0)}
+                     for k in ("bf16split", "bf16split8", "fp32", "bf16", "fp8") for w in (1, 0)}
         result["accuracy"] = accuracy_comparison(goat, synthetic, torch, acc_forms, args.accuracy_seeds)
         log(f"accuracy on the n=1500 SBM: {result['accuracy']['rho']}")
     if not args.no_learned and rank == 0:

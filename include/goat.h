@@ -91,7 +91,14 @@ enum {
     /* the first product (C1 = B Q^T) in E4M3 (B exact, Q rounded under one
      * power-of-two scale, twice the BF16 rate), C1 written as two BF16 terms for a
      * BF16 second product: 2.5 BF16 MMA passes per gradient. */
-    GOAT_PREC_FP8_SPLIT = 4
+    GOAT_PREC_FP8_SPLIT = 4,
+    /* the split form with the low term of Q B in E4M3: C1 = B Q^T as hi + lo (BF16),
+     * both multiplied by one power of two s (exact) so that s lo fits E4M3 (|lo| is at
+     * most 2^-9 |hi|); the second product runs the hi term in BF16 and the lo term in
+     * E4M3 against A in E4M3 (twice the BF16 rate) into one FP32 accumulator, then
+     * divides by s.  The lo term keeps about 4 of its bits: Q B is carried to about
+     * 2^-13 relative instead of 2^-9 (BF16) or 2^-17 (split).  2.5 BF16 MMA passes. */
+    GOAT_PREC_BF16_SPLIT8 = 5
 };
 
 /* direction step of each Frank-Wolfe iteration (goat_params.direction) */

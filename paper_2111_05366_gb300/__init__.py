@@ -35,6 +35,7 @@ GOAT_PREC_FP32 = 1
 GOAT_PREC_FP8 = 2
 GOAT_PREC_BF16_SPLIT = 3
 GOAT_PREC_FP8_SPLIT = 4
+GOAT_PREC_BF16_SPLIT8 = 5
 GOAT_DIR_LOT = 0  # GOAT (Alg. 3): entropic OT direction
 GOAT_DIR_LAP = 1  # FAQ (Alg. 1): exact linear-assignment direction
 GOAT_TRACE_MAX = 256

@@ -43,6 +43,7 @@ struct Plan {
     int terms;  // BF16 terms of Q (2 in the FP32-accurate form)
     int tc;     // BF16 terms of C1 (2 in the FP32-accurate and the split-intermediate forms)
     bool q8;    // first product in E4M3 (B and Q), second in BF16 over C1's two terms
+    bool lo8;   // second product: C1's hi term in BF16, its lo term in E4M3 against A in E4M3
     int ld8;    // E4M3 row width of Q (multiple of 128; equal to ld for directed graphs)
     int parts;  // 1, or 2 for directed graphs: A16 = [A | A^T], B16 = [B | B^T], C1 = [C1 | C1']
     int ldm;    // K extent of the seed term (multiple of 64)
@@ -68,11 +69,13 @@ static Plan make_plan(const Shape &sh, int dtype, int precision, int need) {
     w.ld = sh.dir ? (int)round_up(n, 128) : operand_ld(n);
     w.ld8 = (int)round_up(n, 128);  // an E4M3 stage holds 128 elements of K
     w.terms = precision == GOAT_PREC_FP32 ? 2 : 1;
-    w.tc = (precision == GOAT_PREC_FP32 || precision == GOAT_PREC_BF16_SPLIT || precision == GOAT_PREC_FP8_SPLIT)
+    w.tc = (precision == GOAT_PREC_FP32 || precision == GOAT_PREC_BF16_SPLIT || precision == GOAT_PREC_FP8_SPLIT ||
+            precision == GOAT_PREC_BF16_SPLIT8)
                ? 2
                : 1;
     w.q8 = precision == GOAT_PREC_FP8_SPLIT;  // 8-bit first product only
     w.fp8 = precision == GOAT_PREC_FP8;
+    w.lo8 = precision == GOAT_PREC_BF16_SPLIT8;  // second product's low term in E4M3
     w.ldm = sh.m > 0 ? (int)round_up((int64_t)sh.m * w.parts, 64) : 0;
     w.state = take(sizeof(DevState));
     w.cost = take(16 * sizeof(double));  // [0,3) u64 sums, [3,6) f64 sums, [6] assignment cost, [7,10) LAP bound
@@ -89,6 +92,13 @@ static Plan make_plan(const Shape &sh, int dtype, int precision, int need) {
             w.Q8 = take((size_t)n * w.ld8);
             w.C8 = take((size_t)n * row8);
             w.f8s = take(4 * sizeof(float));  // [0] max|Q| bits, [1] 1/s_Q, [2] max|C1| bits, [3] 1/s_C1
+        }
+        if (w.lo8) {
+            // A in E4M3 and the low term of C1 in E4M3, both K-major over [A | A^T]
+            const size_t row8 = sh.dir ? 2 * (size_t)w.ld : (size_t)w.ld8;
+            w.A8 = take((size_t)n * row8);
+            w.C8 = take((size_t)n * row8);
+            w.f8s = take(4 * sizeof(float));  // [2] max|C1| bits, [3] 1/s
         }
         w.deg = take((size_t)4 * n * 4);  // out-degrees of A, B, in-degrees of A, B (directed)
         if (sh.m > 0) {
@@ -374,6 +384,14 @@ static int gradient_bf16(const Plan &w, const Scratch &ws, float scale2, float *
     }
     if (between) cudaEventRecord(between, s);
 
+    if (w.lo8) {
+        // C1's lo term to E4M3 (hi scaled by the same power of two); the scale's inverse
+        // goes to the second product's epilogue
+        float *sc = ws.at<float>(w.f8s);
+        GOAT_TRY(split_lo_to_e4m3(ws.at<__nv_bfloat16>(w.C1), n, w.ld, w.parts, ws.at<uint8_t>(w.C8),
+                                  w.dir ? w.ld : w.ld8, reinterpret_cast<unsigned *>(sc + 2), sc + 3, s));
+    }
+
     // K runs over [A | A^T] (period parts*ld) against C1's row: term t, part p at
     // offset (t * parts + p) ld, so position k meets A for p = 0 and A^T for p = 1
     GemmCall c2 = c1;
@@ -391,6 +409,18 @@ static int gradient_bf16(const Plan &w, const Scratch &ws, float scale2, float *
     c2.ld_out = n;
     c2.out_b16 = nullptr;
     c2.out_cols = n;
+    if (w.lo8) {
+        // BF16 over the hi term, then E4M3 over the lo term against A in E4M3
+        const long long row8 = w.dir ? 2LL * w.ld : w.ld8;
+        c2.k_total = w.parts * w.ld;
+        c2.scale_dev = ws.at<float>(w.f8s) + 3;
+        c2.X8 = ws.at<uint8_t>(w.A8);
+        c2.x8_stride = row8;
+        c2.kx8_period = (int)row8;
+        c2.Y8 = ws.at<uint8_t>(w.C8);
+        c2.y8_stride = row8;
+        c2.k8_total = (int)row8;
+    }
     return run(c2);
 }
 
@@ -425,14 +455,14 @@ static int prepare_operands(const AdjView &A, const AdjView &B, const Plan &w, c
                 GOAT_TRY(adj_col_sums(B, m, m, n, n, deg + 3 * (size_t)n, s));
             }
         }
-        if (w.fp8 || w.q8) {
+        if (w.fp8 || w.q8 || w.lo8) {
             const int width = w.dir ? w.ld : w.ld8;
             const long long row8 = w.dir ? 2LL * w.ld : w.ld8;
             GOAT_TRY(adj_to_e4m3(A, m, m, n, n, ws.at<uint8_t>(w.A8), width, row8, s));
-            GOAT_TRY(adj_to_e4m3(B, m, m, n, n, ws.at<uint8_t>(w.B8), width, row8, s));
+            if (!w.lo8) GOAT_TRY(adj_to_e4m3(B, m, m, n, n, ws.at<uint8_t>(w.B8), width, row8, s));
             if (w.dir) {
                 GOAT_TRY(adj_to_e4m3_t(A, m, m, n, n, ws.at<uint8_t>(w.A8) + w.ld, w.ld, row8, s));
-                GOAT_TRY(adj_to_e4m3_t(B, m, m, n, n, ws.at<uint8_t>(w.B8) + w.ld, w.ld, row8, s));
+                if (!w.lo8) GOAT_TRY(adj_to_e4m3_t(B, m, m, n, n, ws.at<uint8_t>(w.B8) + w.ld, w.ld, row8, s));
             }
         }
     }
@@ -743,7 +773,7 @@ static goat_params resolve_params(const goat_params *p) {
 
 static bool valid_precision(int p) {
     return p == GOAT_PREC_BF16 || p == GOAT_PREC_FP32 || p == GOAT_PREC_FP8 || p == GOAT_PREC_BF16_SPLIT ||
-           p == GOAT_PREC_FP8_SPLIT;
+           p == GOAT_PREC_FP8_SPLIT || p == GOAT_PREC_BF16_SPLIT8;
 }
 
 // The solve's shape from its parameters; false if they do not fit n.

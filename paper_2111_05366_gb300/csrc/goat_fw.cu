@@ -151,6 +151,56 @@ __global__ void __launch_bounds__(256) k_bf16_to_e4m3(const __nv_bfloat16 *__res
     }
 }
 
+// The split intermediate C1 = hi + lo (BF16 terms, rows of `parts` hi blocks then
+// `parts` lo blocks of ld elements, row stride cs) prepared for a second product
+// whose lo term is 8-bit: with amax = max|C1| (so max|hi| <= amax, and |lo| is at
+// most half a BF16 unit of hi, <= 2^-8 |hi|), s is the largest power of two with
+// s amax 2^-8 <= 448; lo -> E4M3(s lo) in C8 (rows of `parts` blocks of w8 bytes,
+// zero beyond ld), hi -> s hi in place (exact: a power of two), inv_scale <- 1/s.
+// One thread per 16 output bytes; ld is a multiple of 64, so a chunk never
+// straddles a block edge.
+__global__ void __launch_bounds__(256) k_split_lo_to_e4m3(__nv_bfloat16 *__restrict__ C1, int rows, int ld,
+                                                          int parts, long long cs, uint8_t *__restrict__ C8, int w8,
+                                                          const unsigned *amax_bits, float *inv_scale) {
+    const float amax = __uint_as_float(*amax_bits);
+    const float q = amax > 0.0f ? (448.0f * 256.0f) / amax : 1.0f;
+    const float sc = __uint_as_float(__float_as_uint(q) & 0x7F800000u);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *inv_scale = 1.0f / sc;
+    const int cpr = parts * w8 / 16;  // 16-byte output chunks per row
+    const long long total = (long long)rows * cpr;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / cpr), jc = (int)(t - (long long)i * cpr) * 16;
+        const int part = jc / w8, j = jc - part * w8;
+        uint4 out = make_uint4(0u, 0u, 0u, 0u);
+        if (j < ld) {
+            __nv_bfloat16 *hi = C1 + (long long)i * cs + (long long)part * ld + j;
+            const __nv_bfloat16 *lo = C1 + (long long)i * cs + (long long)(parts + part) * ld + j;
+            const uint4 l0 = __ldg(reinterpret_cast<const uint4 *>(lo)), l1 = __ldg(reinterpret_cast<const uint4 *>(lo) + 1);
+            const unsigned w[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+            unsigned b[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                b[k] = e4m3x2(__uint_as_float(w[k] << 16) * sc, __uint_as_float(w[k] & 0xFFFF0000u) * sc);
+            out = make_uint4(b[0] | (b[1] << 16), b[2] | (b[3] << 16), b[4] | (b[5] << 16), b[6] | (b[7] << 16));
+            uint4 *h4 = reinterpret_cast<uint4 *>(hi);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                uint4 h = h4[u];
+                unsigned hw[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const __nv_bfloat162 v =
+                        __floats2bfloat162_rn(__uint_as_float(hw[k] << 16) * sc, __uint_as_float(hw[k] & 0xFFFF0000u) * sc);
+                    hw[k] = *reinterpret_cast<const unsigned *>(&v);
+                }
+                h4[u] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            }
+        }
+        *reinterpret_cast<uint4 *>(C8 + (long long)i * parts * w8 + jc) = out;
+    }
+}
+
 // Counts entries with A[i][j] != A[j][i] (32 x 32 tiles through shared memory).
 template <typename T>
 __global__ void k_count_asym(const T *__restrict__ A, int n, int *__restrict__ count) {
@@ -787,6 +837,18 @@ int bf16_to_e4m3(const __nv_bfloat16 *X, int rows, int ld_src, uint8_t *X8, int 
     k_absmax_bf16<<<grid_for((long long)rows * ld_src / 8), 256, 0, s>>>(X, (long long)rows * ld_src, amax_bits);
     k_bf16_to_e4m3<<<grid_for((long long)rows * (ld8 / 16)), 256, 0, s>>>(X, rows, ld_src, X8, ld8, amax_bits,
                                                                           inv_scale);
+    return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
+}
+
+int split_lo_to_e4m3(__nv_bfloat16 *C1, int rows, int ld, int parts, uint8_t *C8, int w8, unsigned *amax_bits,
+                     float *inv_scale, cudaStream_t s) {
+    if ((ld % 64) || (w8 % 128) || w8 < ld) return GOAT_ERR_INVALID_ARG;
+    note_launches(2);
+    const long long cs = 2LL * parts * ld;
+    cudaMemsetAsync(amax_bits, 0, sizeof(unsigned), s);
+    k_absmax_bf16<<<grid_for((long long)rows * cs / 8), 256, 0, s>>>(C1, (long long)rows * cs, amax_bits);
+    k_split_lo_to_e4m3<<<grid_for((long long)rows * parts * (w8 / 16)), 256, 0, s>>>(C1, rows, ld, parts, cs, C8, w8,
+                                                                                     amax_bits, inv_scale);
     return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
 }
 

@@ -20,11 +20,14 @@
 // runs over fewer steps, and the chunks are added in the epilogue with
 // round-to-nearest FP32.
 //
-// The same kernel runs the 8-bit form (FP8 = true): E4M3 operands, kind::f8f6f4.
-// A stage then holds 128 elements of K instead of 64 -- the same 128 bytes per
-// swizzled row, so the shared-memory layout, the descriptors and their 32-byte K
-// steps are unchanged; only the element type, the K extent per stage and the
-// instruction kind differ.
+// The same kernel runs the 8-bit form (KIND = KIND_E4M3): E4M3 operands,
+// kind::f8f6f4.  A stage then holds 128 elements of K instead of 64 -- the same 128
+// bytes per swizzled row, so the shared-memory layout, the descriptors and their
+// 32-byte K steps are unchanged; only the element type, the K extent per stage and
+// the instruction kind differ.  KIND_MIXED runs both in one accumulator: the first
+// num_kb_hi K blocks from the BF16 maps (kind::f16), the rest from a second pair of
+// E4M3 maps (kind::f8f6f4) -- the second product of the split form whose low term
+// is 8-bit.
 //
 // Kernel structure (one persistent CTA per SM, 192 threads):
 //   warp 0      TMA producer: X tile 128x64 and Y tile 256x64 per stage (BF16), 4 stages
@@ -42,6 +45,7 @@
 namespace goat {
 
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int KIND_BF16 = 0, KIND_E4M3 = 1, KIND_MIXED = 2;
 constexpr uint32_t TILE_X_BYTES = BM * BK * 2;
 constexpr uint32_t TILE_Y_BYTES = BN * BK * 2;
 constexpr uint32_t STAGE_BYTES = TILE_X_BYTES + TILE_Y_BYTES;
@@ -53,7 +57,9 @@ constexpr size_t GEMM_SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
 struct GemmParams {
     int M, N;            // output rows (from X) and columns (from Y)
     int kx_period;       // X is read at k mod kx_period (multiple of BK)
-    int num_kb;          // K extent / BK
+    int num_kb;          // K blocks (stages) of the launch
+    int num_kb_hi;       // KIND_MIXED: the first num_kb_hi blocks are BF16 (64 elements), the rest E4M3 (128)
+    int kx8_period;      // KIND_MIXED: period of the E4M3 X operand's K (multiple of 128)
     int k_offset_kb;     // first K block of this launch (K positions k_offset_kb * BK + ...)
     const float *addend; // FP32 matrix added in the epilogue (nullable), ld_addend, columns < addend_cols
     long long ld_addend;
@@ -213,9 +219,11 @@ __device__ __forceinline__ void store_tile_row(const GemmParams &p, const TileJo
     }
 }
 
-template <bool GROUPED, bool FP8>
+template <bool GROUPED, int KIND>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
-    k_gemm_xyT(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, const GemmParams p) {
+    k_gemm_xyT(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
+               const __grid_constant__ CUtensorMap tmX8, const __grid_constant__ CUtensorMap tmY8, const GemmParams p) {
+    constexpr bool FP8 = KIND == KIND_E4M3;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * STAGE_BYTES);
@@ -248,6 +256,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     if (warp == 0 && lane == 0) {
         prefetch_tmap(&tmX);
         prefetch_tmap(&tmY);
+        if constexpr (KIND == KIND_MIXED) {
+            prefetch_tmap(&tmX8);
+            prefetch_tmap(&tmY8);
+        }
     }
     if (warp == 1) {
         tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
@@ -274,10 +286,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                         break;
                     }
                     const uint32_t sx = sbase + stage * STAGE_BYTES;
-                    const int kk = (p.k_offset_kb + kb) * (FP8 ? 2 * BK : BK);  // K elements per stage: 128 bytes
                     mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
-                    tma_load_2d(sx, &tmX, full_bar(stage), kk % p.kx_period, job.x_row);
-                    tma_load_2d(sx + TILE_X_BYTES, &tmY, full_bar(stage), kk, job.y_row);
+                    if (KIND == KIND_MIXED && kb >= p.num_kb_hi) {
+                        const int kk = (kb - p.num_kb_hi) * 2 * BK;  // E4M3 block: 128 elements = 128 bytes
+                        tma_load_2d(sx, &tmX8, full_bar(stage), kk % p.kx8_period, job.x_row);
+                        tma_load_2d(sx + TILE_X_BYTES, &tmY8, full_bar(stage), kk, job.y_row);
+                    } else {
+                        const int kk = (p.k_offset_kb + kb) * (FP8 ? 2 * BK : BK);  // K elements per stage: 128 bytes
+                        tma_load_2d(sx, &tmX, full_bar(stage), kk % p.kx_period, job.x_row);
+                        tma_load_2d(sx + TILE_X_BYTES, &tmY, full_bar(stage), kk, job.y_row);
+                    }
                     issued_mask |= 1u << stage;
                     issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
                     if (++stage == STAGES) {
@@ -295,6 +313,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         const uint32_t idesc = FP8 ? idesc_e4m3_f32(BM, BN) : idesc_bf16_f32(BM, BN);
+        const uint32_t idesc8 = idesc_e4m3_f32(BM, BN);
         int stage = 0;
         uint32_t phase = 0;
         int acc = 0;
@@ -319,11 +338,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 if (lane == 0) {
                     const uint32_t sx = sbase + stage * STAGE_BYTES;
                     const uint32_t sy = sx + TILE_X_BYTES;
+                    const bool e4m3 = FP8 || (KIND == KIND_MIXED && kb >= p.num_kb_hi);
 #pragma unroll
                     for (int k = 0; k < BK / 16; ++k) {  // 32 bytes of K per instruction
-                        if constexpr (FP8)
-                            umma_f8(d_tmem, smem_desc_sw128(sx + 32u * k), smem_desc_sw128(sy + 32u * k), idesc,
-                                    (kb | k) != 0 ? 1u : 0u);
+                        if (e4m3)
+                            umma_f8(d_tmem, smem_desc_sw128(sx + 32u * k), smem_desc_sw128(sy + 32u * k),
+                                    FP8 ? idesc : idesc8, (kb | k) != 0 ? 1u : 0u);
                         else
                             umma_bf16(d_tmem, smem_desc_sw128(sx + 32u * k), smem_desc_sw128(sy + 32u * k), idesc,
                                       (kb | k) != 0 ? 1u : 0u);
@@ -436,13 +456,16 @@ static int prepare_launch() {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
-        attr_err = cudaFuncSetAttribute(k_gemm_xyT<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        attr_err = cudaFuncSetAttribute(k_gemm_xyT<false, KIND_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)GEMM_SMEM_BYTES);
         if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute(k_gemm_xyT<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            attr_err = cudaFuncSetAttribute(k_gemm_xyT<true, KIND_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)GEMM_SMEM_BYTES);
         if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute(k_gemm_xyT<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            attr_err = cudaFuncSetAttribute(k_gemm_xyT<false, KIND_E4M3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)GEMM_SMEM_BYTES);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(k_gemm_xyT<false, KIND_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)GEMM_SMEM_BYTES);
     });
     return (attr_err != cudaSuccess || g_sm_count <= 0) ? GOAT_ERR_CUDA : GOAT_OK;
@@ -492,10 +515,25 @@ int gemm_xyT(const GemmCall &c, cudaStream_t stream) {
     p.err = c.err;
     const int tiles = p.tiles_m * p.tiles_n;
     const int grid = tiles < sm_count ? tiles : sm_count;
-    if (c.fp8)
-        k_gemm_xyT<false, true><<<grid, GEMM_THREADS, GEMM_SMEM_BYTES, stream>>>(mx, my, p);
-    else
-        k_gemm_xyT<false, false><<<grid, GEMM_THREADS, GEMM_SMEM_BYTES, stream>>>(mx, my, p);
+    if (c.X8) {
+        // mixed: the BF16 maps above cover K [0, k_total), the E4M3 maps K8 [0, k8_total)
+        if (c.fp8 || c.k_begin || c.addend || c.k8_total < 1 || (c.k8_total % (2 * BK)) || c.kx8_period < 1 ||
+            (c.kx8_period % (2 * BK)))
+            return GOAT_ERR_INVALID_ARG;
+        CUtensorMap mx8, my8;
+        st = make_map(&mx8, c.X8, (uint64_t)c.kx8_period, (uint64_t)c.x_rows, (uint64_t)c.x8_stride, BM, true);
+        if (st) return st;
+        st = make_map(&my8, c.Y8, (uint64_t)c.k8_total, (uint64_t)c.y_rows, (uint64_t)c.y8_stride, BN, true);
+        if (st) return st;
+        p.num_kb_hi = p.num_kb;
+        p.num_kb += c.k8_total / (2 * BK);
+        p.kx8_period = c.kx8_period;
+        k_gemm_xyT<false, KIND_MIXED><<<grid, GEMM_THREADS, GEMM_SMEM_BYTES, stream>>>(mx, my, mx8, my8, p);
+    } else if (c.fp8) {
+        k_gemm_xyT<false, KIND_E4M3><<<grid, GEMM_THREADS, GEMM_SMEM_BYTES, stream>>>(mx, my, mx, my, p);
+    } else {
+        k_gemm_xyT<false, KIND_BF16><<<grid, GEMM_THREADS, GEMM_SMEM_BYTES, stream>>>(mx, my, mx, my, p);
+    }
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
 }
@@ -521,7 +559,7 @@ int gemm_grouped(const GemmGroupCall &c, cudaStream_t stream) {
     p.num_items = c.num_items;
     p.descs = c.descs;
     const int grid = c.num_items < g_sm_count ? c.num_items : g_sm_count;
-    k_gemm_xyT<true, false><<<grid, GEMM_THREADS, GEMM_SMEM_BYTES, stream>>>(mx, my, p);
+    k_gemm_xyT<true, KIND_BF16><<<grid, GEMM_THREADS, GEMM_SMEM_BYTES, stream>>>(mx, my, mx, my, p);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
 }

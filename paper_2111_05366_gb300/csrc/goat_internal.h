@@ -41,6 +41,15 @@ struct GemmCall {
     const float *addend;     // FP32 matrix added to the result in the epilogue (nullable; may be out_f32 itself)
     long long ld_addend;
     int addend_cols;         // columns of the addend (later output columns add nothing)
+    // mixed launch (X8 non-null): after the BF16 K range above, K8 more positions of
+    // E4M3 operands X8 (period kx8_period, row stride x8_stride) and Y8 (row stride
+    // y8_stride) into the same accumulator; BF16 only above, no k_begin or addend
+    const void *X8;
+    long long x8_stride;
+    int kx8_period;
+    const void *Y8;
+    long long y8_stride;
+    int k8_total;            // multiple of 128
 };
 
 int gemm_xyT(const GemmCall &c, cudaStream_t stream);
@@ -102,6 +111,10 @@ int adj_to_bf16_t(const AdjView &v, int r0, int c0, int rows, int cols, __nv_bfl
 int adj_to_e4m3_t(const AdjView &v, int r0, int c0, int rows, int cols, uint8_t *dst, int width, long long stride,
                   cudaStream_t s);
 int adj_col_sums(const AdjView &v, int r0, int c0, int rows, int cols, float *out, cudaStream_t s);
+// The split intermediate's lo term -> E4M3 (and its hi term scaled to match) for the
+// second product of GOAT_PREC_BF16_SPLIT8; inv_scale (device) receives 1/s.
+int split_lo_to_e4m3(__nv_bfloat16 *C1, int rows, int ld, int parts, uint8_t *C8, int w8, unsigned *amax_bits,
+                     float *inv_scale, cudaStream_t s);
 int bf16_to_e4m3(const __nv_bfloat16 *X, int rows, int ld_src, uint8_t *X8, int ld8, unsigned *amax_bits,
                  float *inv_scale, cudaStream_t s);
 int count_asym(const void *A, int dtype, int n, int *count_dev, cudaStream_t s);

@@ -101,4 +101,7 @@ def test_workspace_sizes_grow_with_the_form(lib_path):
         ld, ld8 = -(-n // 64) * 64, -(-n // 128) * 128
         assert f32 - b16 >= 2 * n * ld * 2 - 1024  # Xq and C1 gain a second BF16 term (256-byte rounding)
         assert f8 - b16 >= 4 * n * ld8 - 1024      # A8, B8, Q8, C8
+        sp = goat.workspace_bytes(n, goat.GOAT_DTYPE_U8, goat.GOAT_PREC_BF16_SPLIT)
+        sp8 = goat.workspace_bytes(n, goat.GOAT_DTYPE_U8, goat.GOAT_PREC_BF16_SPLIT8)
+        assert sp8 - sp >= 2 * n * ld8 - 1024      # A8 and the lo term's C8
         assert goat.workspace_bytes(n, goat.GOAT_DTYPE_U8, goat.GOAT_PREC_BF16, host=True) > b16

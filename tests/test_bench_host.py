@@ -35,12 +35,13 @@ def test_committed_8bit_traffic_matches_the_current_product_kernel():
     assert t == pytest.approx(36.70e9, rel=1e-3), "k_gemm_xyT changed since profiles/k_gemm_xyT_fp8_traffic.txt was captured"
 
 
-def test_committed_split_form_traffic_matches_the_current_product_kernel():
-    # the timed (split-intermediate BF16) form's roofline.traffic: the mean of its two
-    # products' DRAM bytes at n = 32768 (K = n, then K = 2n)
+@pytest.mark.parametrize("name,gb", [("k_gemm_xyT_traffic.txt", 70.35), ("k_gemm_xyT_split_traffic.txt", 151.47),
+                                     ("k_gemm_xyT_split8_traffic.txt", 96.87)])
+def test_committed_traffic_of_every_timed_form_matches_the_current_product_kernel(name, gb):
+    # each form's roofline.traffic: the mean of its two products' DRAM bytes at n = 32768
     bench = _bench()
-    t = bench.gemm_traffic_per_launch(32768, "k_gemm_xyT_split_traffic.txt")
-    assert t == pytest.approx(189.01e9, rel=1e-3), "k_gemm_xyT changed since the split-form capture"
+    t = bench.gemm_traffic_per_launch(32768, name)
+    assert t == pytest.approx(gb * 1e9, rel=1e-3), f"k_gemm_xyT changed since profiles/{name} was captured"
 
 
 def test_traffic_is_dropped_when_the_kernel_source_changes(tmp_path):

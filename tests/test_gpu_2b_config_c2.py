@@ -33,7 +33,8 @@ def c2():
 
 
 # (form, bound on max |P - P_oracle| / max P_oracle, or None: stated only)
-FORMS = [(goat.GOAT_PREC_FP32, 1e-4), (goat.GOAT_PREC_BF16_SPLIT, 1e-2), (goat.GOAT_PREC_BF16, None),
+FORMS = [(goat.GOAT_PREC_FP32, 1e-4), (goat.GOAT_PREC_BF16_SPLIT, 1e-2), (goat.GOAT_PREC_BF16_SPLIT8, 1e-2),
+         (goat.GOAT_PREC_BF16, None),
          (goat.GOAT_PREC_FP8, None)]
 
 

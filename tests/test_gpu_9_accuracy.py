@@ -55,7 +55,7 @@ def mean_accuracy(pairs, precision, warm):
     return float(np.mean(accs))
 
 
-@pytest.mark.parametrize("precision", [goat.GOAT_PREC_FP32, goat.GOAT_PREC_BF16_SPLIT])
+@pytest.mark.parametrize("precision", [goat.GOAT_PREC_FP32, goat.GOAT_PREC_BF16_SPLIT, goat.GOAT_PREC_BF16_SPLIT8])
 @pytest.mark.parametrize("warm", [0, 1])
 def test_accurate_forms_within_one_point_of_oracle(pairs, precision, warm):
     ref = oracle_accuracy()
