@@ -279,6 +279,15 @@ GOAT_API int goat_line_search(const float *G, const float *G_Q, const float *P, 
 GOAT_API int goat_fw_update(float *P, float *G, const float *Q, const float *G_Q, int n, double alpha, goat_stream_t stream);
 
 /*
+ * goat_entropic_eps -- the entropic weight of Alg. 2 as goat_match chooses it
+ * (the paper's lambda read as eps = 1 / lambda, relative to the cost's scale):
+ *   eps = eps_rel * max|G|, or 1 when G == 0 (every doubly stochastic Q is then optimal).
+ *   G device n x n float; eps_out HOST float.  Allocates 4 bytes with cudaMallocAsync
+ *   on `stream` and waits for the stream.  GOAT_ERR_NAN for a non-finite entry.
+ */
+GOAT_API int goat_entropic_eps(const float *G, int n, float eps_rel, float *eps_out, goat_stream_t stream);
+
+/*
  * goat_project -- the final linear assignment (Alg. 3 return line):
  * perm = argmax (maximize = 1) or argmin (0) of sum_i M[i][perm i] over permutations.
  * Exact: the entries are quantised to 64-bit integers (40 bits below the largest
@@ -425,6 +434,10 @@ GOAT_API int goat_sinkhorn_noalloc(const float *G, int n, float eps, float tol, 
 GOAT_API int goat_dual_features(const float *G, const void *A, const void *B, int n, int dtype_AB, float eps,
                                 float *feats, void *workspace, size_t workspace_bytes, goat_stream_t stream);
 GOAT_API int goat_mlp_forward(const void *weights_bf16, const float *x, int N, float *y, goat_stream_t stream);
+/* goat_dual_targets -- the training targets of a solve's duals f, g (device, n floats
+ * each) at weight eps: t_out (device, 2n floats) = [f/eps - mean(f/eps),
+ * g/eps - mean(g/eps)] (the duals are defined up to f + c, g - c), means in FP64. */
+GOAT_API int goat_dual_targets(const float *f, const float *g, int n, float eps, float *t_out, goat_stream_t stream);
 GOAT_API int goat_mlp_train_step(float *master, float *adam_state, void *weights_bf16, const float *x,
                                  const float *t, int N, float lr, int step, float *loss_out, float *grad_out,
                                  goat_stream_t stream);

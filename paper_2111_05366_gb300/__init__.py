@@ -46,7 +46,8 @@ EXPORTED = ["goat_default_params", "goat_strerror", "goat_workspace_bytes", "goa
             "goat_gradient", "goat_gradient_ex", "goat_sinkhorn", "goat_line_search", "goat_fw_update", "goat_project",
             "goat_objective", "goat_gemm_bf16_xyT", "goat_sinkhorn_noalloc", "goat_match_batched",
             "goat_workspace_bytes_batched", "goat_dual_features", "goat_mlp_forward", "goat_mlp_train_step",
-            "goat_mlp_warm_start", "goat_lap_default_options", "goat_project_ex"]
+            "goat_mlp_warm_start", "goat_lap_default_options", "goat_project_ex", "goat_entropic_eps",
+            "goat_dual_targets"]
 
 
 class GoatError(RuntimeError):
@@ -124,6 +125,8 @@ def load():
             "goat_line_search": (_i, [_vp, _vp, _vp, _vp, _i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d),
                                       ctypes.POINTER(_d), _vp, ctypes.c_size_t, _vp]),
             "goat_fw_update": (_i, [_vp, _vp, _vp, _vp, _i, _d, _vp]),
+            "goat_entropic_eps": (_i, [_vp, _i, _f, ctypes.POINTER(_f), _vp]),
+            "goat_dual_targets": (_i, [_vp, _vp, _i, _f, _vp, _vp]),
             "goat_project": (_i, [_vp, _i, _i, _vp, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp, ctypes.c_size_t,
                                   _vp]),
             "goat_lap_default_options": (None, [ctypes.POINTER(goat_lap_options)]),
@@ -335,6 +338,27 @@ def goat_fw_update(P, G, Q, G_Q, alpha: float):
                               _dev(Q, torch.float32, sh, "Q"), _dev(G_Q, torch.float32, sh, "G_Q"), n, float(alpha),
                               _stream())
     _check(r, "goat_fw_update")
+
+
+def goat_entropic_eps(G, eps_rel: float = 0.03) -> float:
+    """The entropic weight goat_match uses for cost G: eps_rel * max|G| (1 if G == 0)."""
+    torch = _torch()
+    n = G.shape[0]
+    e = _f()
+    r = load().goat_entropic_eps(_dev(G, torch.float32, (n, n), "G"), n, float(eps_rel), ctypes.byref(e), _stream())
+    _check(r, "goat_entropic_eps")
+    return e.value
+
+
+def goat_dual_targets(f, g, eps: float):
+    """Training targets [f/eps - mean, g/eps - mean] (2n floats) of converged duals."""
+    torch = _torch()
+    n = f.shape[0]
+    t = torch.empty(2 * n, dtype=torch.float32, device=f.device)
+    r = load().goat_dual_targets(_dev(f, torch.float32, (n,), "f"), _dev(g, torch.float32, (n,), "g"), n,
+                                 float(eps), _dev(t, torch.float32, (2 * n,), "t"), _stream())
+    _check(r, "goat_dual_targets")
+    return t
 
 
 def goat_project(M, maximize: bool = True, allow_uncertified: bool = False):

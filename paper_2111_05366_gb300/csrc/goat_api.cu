@@ -969,6 +969,30 @@ int goat_line_search(const float *G, const float *G_Q, const float *P, const flo
     return hs.error;
 }
 
+int goat_entropic_eps(const float *G, int n, float eps_rel, float *eps_out, goat_stream_t stream) {
+    if (!G || !eps_out || n < 1 || !(eps_rel > 0.0f)) return GOAT_ERR_INVALID_ARG;
+    GOAT_TRY(device_ok());
+    cudaStream_t s = (cudaStream_t)stream;
+    int *pinned = pinned_words();
+    if (!pinned) return GOAT_ERR_CUDA;
+    unsigned *bits = nullptr;
+    GOAT_TRY(cuda_status(cudaMallocAsync((void **)&bits, sizeof(unsigned), s)));
+    cudaMemsetAsync(bits, 0, sizeof(unsigned), s);
+    absmax(G, (long long)n * n, bits, s);
+    cudaMemcpyAsync(pinned, bits, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(bits, s);
+    GOAT_TRY(cuda_status(cudaStreamSynchronize(s)));
+    float gm;
+    std::memcpy(&gm, pinned, sizeof(float));
+    if (!(gm == gm) || std::isinf(gm)) return GOAT_ERR_NAN;
+    // the rule of k_sk_begin: eps_rel max|G|, and 1 when G == 0 (every doubly
+    // stochastic Q is then optimal)
+    float e = eps_rel * gm;
+    if (!(e > 0.0f)) e = 1.0f;
+    *eps_out = e;
+    return GOAT_OK;
+}
+
 int goat_fw_update(float *P, float *G, const float *Q, const float *G_Q, int n, double alpha, goat_stream_t stream) {
     if (!P || !G || !Q || !G_Q || n < 1 || !(alpha >= 0.0 && alpha <= 1.0)) return GOAT_ERR_INVALID_ARG;
     GOAT_TRY(device_ok());

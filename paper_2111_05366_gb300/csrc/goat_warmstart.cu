@@ -355,6 +355,34 @@ int mlp_forward(const __nv_bfloat16 *w, const float *x, int N, float *y, cudaStr
     return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
 }
 
+// Training targets of the network: t = [f / eps - mean(f / eps), g / eps - mean(g / eps)]
+// (the duals are defined up to f + c, g - c).  One CTA; the means are FP64 sums in a
+// fixed order (strided per thread, then a tree), so t does not depend on timing.
+__global__ void __launch_bounds__(1024) k_dual_targets(const float *__restrict__ f, const float *__restrict__ g, int n,
+                                                       float eps, float *__restrict__ t) {
+    __shared__ double sf[1024], sg[1024];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        a += (double)f[i] / eps;
+        b += (double)g[i] / eps;
+    }
+    sf[threadIdx.x] = a;
+    sg[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sf[threadIdx.x] += sf[threadIdx.x + o];
+            sg[threadIdx.x] += sg[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    const double mf = sf[0] / n, mg = sg[0] / n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        t[i] = (float)((double)f[i] / eps - mf);
+        t[n + i] = (float)((double)g[i] / eps - mg);
+    }
+}
+
 // Sets g_j = eps * (MLP prediction of the B-side node j) as the Sinkhorn warm start.
 __global__ void k_scale_duals(const float *__restrict__ y, int n, float eps, float *__restrict__ g) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -429,6 +457,13 @@ int goat_mlp_warm_start(const float *G, const void *A, const void *B, int n, int
     const int st = mlp_warm_start_g(G, A, B, n, dtype_AB, eps, (const __nv_bfloat16 *)weights_bf16, g_out, scratch, s);
     if (own) cudaFreeAsync(scratch, s);
     return st;
+}
+
+int goat_dual_targets(const float *f, const float *g, int n, float eps, float *t_out, goat_stream_t stream) {
+    if (!f || !g || !t_out || n < 1 || !(eps > 0.0f)) return GOAT_ERR_INVALID_ARG;
+    k_dual_targets<<<1, 1024, 0, (cudaStream_t)stream>>>(f, g, n, eps, t_out);
+    note_launches(1);
+    return cudaGetLastError() == cudaSuccess ? GOAT_OK : GOAT_ERR_CUDA;
 }
 
 int goat_mlp_forward(const void *weights_bf16, const float *x, int N, float *y, goat_stream_t stream) {

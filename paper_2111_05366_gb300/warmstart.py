@@ -12,8 +12,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import (GOAT_MLP_PARAMS, goat_dual_features, goat_fw_update, goat_gradient, goat_line_search,
-               goat_mlp_train_step, goat_sinkhorn)
+from . import (GOAT_MLP_PARAMS, goat_dual_features, goat_dual_targets, goat_entropic_eps, goat_fw_update,
+               goat_gradient, goat_line_search, goat_mlp_train_step, goat_sinkhorn)
 from . import synthetic
 
 
@@ -35,15 +35,10 @@ def collect(pairs, fw_steps: int = 3, eps_rel: float = 0.03, sk_tol: float = 1e-
         P = torch.full((n, n), 1.0 / n, dtype=torch.float32, device="cuda")
         G = goat_gradient(A, B, P)
         for _ in range(fw_steps):
-            eps = eps_rel * float(G.abs().max())
-            if not eps > 0:
-                break
+            eps = goat_entropic_eps(G, eps_rel)  # the rule goat_match applies
             f, g, Q, it, res = goat_sinkhorn(G, eps, sk_tol, sk_max_iter, want_Q=True)
-            F = goat_dual_features(G, A, B, eps)
-            tf = f / eps
-            tg = g / eps
-            xs.append(F)
-            ts.append(torch.cat([tf - tf.mean(), tg - tg.mean()]))
+            xs.append(goat_dual_features(G, A, B, eps))
+            ts.append(goat_dual_targets(f, g, eps))
             GQ = goat_gradient(A, B, Q)
             alpha, _, _ = goat_line_search(G, GQ, P, Q)
             goat_fw_update(P, G, Q, GQ, alpha)

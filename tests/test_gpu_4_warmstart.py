@@ -104,3 +104,19 @@ def test_trained_network_beats_cold_start_on_held_out_problems():
     prm = goat.default_params(mlp_weights=wb)
     perm, obj, st = goat.goat_match(torch.from_numpy(gp.A).cuda(), torch.from_numpy(gp.B).cuda(), params=prm)
     assert obj == oracle.objective_perm(gp.A, gp.B, perm)
+
+
+def test_entropic_eps_and_dual_targets_follow_their_definitions():
+    # eps = eps_rel max|G| (float32 product, as the solve computes it), 1 for G = 0;
+    # targets = duals over eps with each side's mean removed
+    rng = np.random.default_rng(8)
+    n = 333
+    G = rng.standard_normal((n, n)).astype(np.float32) * 7.0
+    e = goat.goat_entropic_eps(torch.from_numpy(G).cuda(), 0.03)
+    assert e == float(np.float32(0.03) * np.float32(np.abs(G).max()))
+    assert goat.goat_entropic_eps(torch.zeros((n, n), dtype=torch.float32, device="cuda"), 0.03) == 1.0
+    f = rng.standard_normal(n).astype(np.float32)
+    g = rng.standard_normal(n).astype(np.float32) + 5.0
+    t = goat.goat_dual_targets(torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda(), 0.25).cpu().double().numpy()
+    tf, tg = f.astype(np.float64) / 0.25, g.astype(np.float64) / 0.25
+    np.testing.assert_allclose(t, np.concatenate([tf - tf.mean(), tg - tg.mean()]), rtol=0, atol=1e-5)
