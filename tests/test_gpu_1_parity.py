@@ -381,6 +381,22 @@ def test_match_rejects_asymmetric_input():
     assert e.value.status == goat.GOAT_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("n,weighted", [(300, False), (1000, False), (40, False), (300, True)])
+def test_first_step_from_the_barycenter_matches_oracle(n, weighted):
+    # one FW step from J (the closed-form barycenter gradient, a cold Sinkhorn solve,
+    # the exact step size): the step's iteration count and the relaxed iterate follow
+    # the oracle's, for 0/1 and weighted pairs and below one 128-row tile
+    gp = synthetic.rho_er_pair(n, 0.1, 0.8, seed=n + 11, weighted=weighted)
+    P = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    prm = goat.default_params(precision=goat.GOAT_PREC_FP32, sk_tol=1e-4, sk_max_iter=2000, relaxed_out=P)
+    _, _, st = goat.goat_match(cuda(gp.A), cuda(gp.B), eps_rel=0.03, max_iter=1, tol=0.0, params=prm)
+    ro = oracle.goat(gp.A, gp.B, eps_rel=0.03, max_iter=1, tol=0.0, sk_tol=1e-4, sk_max_iter=2000)
+    assert abs(st["sk_iters"][0] - int(ro["sinkhorn_iters"][0])) <= 1
+    np.testing.assert_allclose(st["alpha"][0], 1.0 - ro["alphas"][0], atol=1e-5)
+    err = np.abs(P.cpu().double().numpy() - ro["P"]).max() / ro["P"].max()
+    assert err <= 1e-4, err
+
+
 def test_match_isomorphic_recovery():
     for seed in range(3):
         gp = synthetic.rho_er_pair(150, 0.1, 1.0, seed=seed)
