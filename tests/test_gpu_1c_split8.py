@@ -58,3 +58,20 @@ def test_split8_match_objective_is_exact():
     perm, obj, st = goat.goat_match(cuda(gp.A), cuda(gp.B), params=prm)
     assert sorted(perm.tolist()) == list(range(400))
     assert obj == oracle.objective_perm(gp.A, gp.B, perm)
+
+
+@pytest.mark.parametrize("directed,seeds", [(1, 0), (0, 30), (1, 20)])
+def test_split8_seeded_and_directed_solves_are_exact(directed, seeds):
+    # the whole solve in the split8 form on the other operand layouts: [A | A^T] rows
+    # (directed) and the unseeded block (seeds); the permutation keeps the seeds and
+    # its objective is the oracle's exact value
+    n = 260
+    make = synthetic.rho_er_digraph_pair if directed else synthetic.rho_er_pair
+    gp = make(n, 0.08, 0.9, seed=31 + seeds)
+    prm = goat.default_params(precision=goat.GOAT_PREC_BF16_SPLIT8, directed=directed, seeds=seeds,
+                              sk_warm_start=1)
+    perm, obj, st = goat.goat_match(cuda(gp.A), cuda(gp.B), params=prm)
+    assert sorted(perm.tolist()) == list(range(n))
+    np.testing.assert_array_equal(perm[:seeds], np.arange(seeds))
+    assert obj == oracle.objective_perm(gp.A, gp.B, perm)
+    assert st["fw_iters"] >= 1
