@@ -20,9 +20,9 @@
 //
 // Scheduling.  Each phase starts with parallel Jacobi rounds (one cooperative
 // launch per phase) while many rows bid, until at most 4 rows bid or the number of
-// bidders has not fallen for 16 rounds; the long tail of a phase (a few rows
-// evicting each other) then runs in Gauss-Seidel order in one CTA, or for
-// n >= 4096 in a cluster of 8 CTAs that split the columns.  Rows that still chase
+// bidders has not fallen for 16 rounds; when they end with at most 4 rows left,
+// that tail (a few rows evicting each other) runs in Gauss-Seidel order in one
+// CTA, or for n >= 4096 in a cluster of 8 CTAs that split the columns.  Rows that chase
 // the last free objects through a large set of near-tied objects (each bid lifts
 // one price by about eps, so closing a gap of D costs about |set| D / eps bids)
 // are left to the next phase, which starts from the prices alone; in the last
@@ -1413,7 +1413,11 @@ int lap_solve(const float *M, int n, int maximize, int32_t *perm_out, void *lap_
         const long long budget = ctl.tail_bids >= 0 ? ctl.tail_bids
                                  : last             ? std::max(4LL * n, 262144LL)
                                                     : std::max((long long)n, 65536LL);
-        if (left > 0 && budget > 0) {
+        // the sequential tail serves the last few rows of a phase; rows the Jacobi rounds
+        // stalled on (near-tied objects, no progress in head_stall rounds) stall it too
+        // and are left to the next phase, or to the searches in the last
+        const bool head_stalled = head_grid > 0 && left > head_threshold;
+        if (left > 0 && budget > 0 && !head_stalled) {
             t0 = clk::now();
             if (use_cluster_tail) {
                 k_lap_tail_cluster<<<LAP_CLUSTER, 256, tail_smem, s>>>(M, n, q, L, eps, budget, stall, st);
