@@ -76,3 +76,26 @@ def test_cpu_baseline_sample_runs_the_oracle_on_every_core_with_one_sinkhorn_cou
     assert r["value"] > 0 and r["value"] == pytest.approx(1.0 / r["seconds_per_fw_iter"])
     assert "6 rows" in r["sample"] and "3 threads" in r["sample"]
     assert bench.host_cores() >= 1
+
+
+def test_form_report_rates_from_the_library_timings():
+    # the per-form figures come from the solves' own stats: FW iterations over the
+    # timed ms, the products' mean launch time, and the Sinkhorn rate on 4 n^2 bytes
+    # per iteration against the measured copy peak and the nominal 7.9 TB/s
+    import numpy as np
+    bench = _bench()
+    n = 32768
+    st = {"fw_iters": 5, "ms_gemm": 560.0, "gemm_launches": 10, "ms_fw": 760.0, "ms_sinkhorn": 170.0,
+          "sk_iters_total": 254, "ms_project": 245.0, "objective": 1.0, "lap_gap": 0.0}
+    truth = np.arange(8)
+    outs = [(truth.copy(), 1.0, st), (truth.copy(), 1.0, st)]
+    peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+    r = bench.form_report(outs, 2000.0, "bf16split8", n, peaks, 2.0e7, truth)
+    assert r["value"] == pytest.approx(10 / 2.0) and r["ms_per_solve"] == pytest.approx(1000.0)
+    assert r["gemm_ms_per_launch"] == pytest.approx(56.0) and r["accuracy"] == 1.0
+    t_it = 340.0 / 508 / 1000.0
+    assert r["sinkhorn_algorithmic_gbs"] == pytest.approx(4.0 * n * n / t_it / 1e9)
+    assert r["sinkhorn_frac_of_hbm_peak"] == pytest.approx(r["sinkhorn_algorithmic_gbs"] / 6800.0)
+    assert r["sinkhorn_frac_of_nominal_hbm"] == pytest.approx(r["sinkhorn_algorithmic_gbs"] / 7900.0)
+    # split8: the second product is 1.5 BF16-equivalent passes
+    assert r["roofline"]["executed_flop_per_launch"] == pytest.approx(2.0 * n ** 3 * 1.25)
